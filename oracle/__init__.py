@@ -1,0 +1,280 @@
+"""CPU ORACLE — test infrastructure only.
+
+A plain, slow, obviously correct CPU implementation of what the method
+computes, in FP64 where floating point is involved. Only tests/, the smoke
+check in __graft_entry__ and bench.py's CPU-baseline leg may import it; the
+library (paper_2504_05808_gb300) never does, and the two share no code.
+
+What it computes (paper: "Fast Sphericity and Roundness approximation in 2D
+and 3D using Local Thickness"):
+
+  dt2(mask)            squared Euclidean distance from each foreground voxel to
+                       the nearest background voxel; outside the array counts
+                       as background. Plain definition (C loops, lt_oracle.c).
+  lt2(dt2, labels)     local thickness, squared: the largest DT2(c) over all
+                       same-label centres c whose inclusive ball
+                       |x - c|^2 <= DT2(c) holds x (Sec. 1; Sec. 4, first
+                       paragraph). Painting from every centre, no pruning.
+  object_stats(...)    per label: V (voxel count, Sec. 4.1 after Eq. 7),
+                       shell voxels (a 4-/6-neighbour outside the object,
+                       Sec. 4.2), sum of LT, sum of LT on the shell, max LT2.
+  sphericity_3d        Eqs. 1, 6-8: spheroid with a = mean LT, c = 3V/(4 pi a^2).
+  sphericity_2d        Eqs. 2, 9-11: ellipse with a = mean LT, b = A/(pi a);
+                       Ramanujan's perimeter P_o and P_c = 2 sqrt(pi A).
+  roundness            Sec. 4.2: mean LT on the shell / max LT.
+
+Readings where the paper is garbled or silent (each is listed in the design doc):
+  * Eqs. 6-7 print e = 1 - c^2/a^2 without a square root; the spheroid's
+    eccentricity is e = sqrt(1 - c^2/a^2) (oblate) and sqrt(1 - a^2/c^2)
+    (prolate). At c = a both give the sphere, 4 pi a^2.
+  * Eq. 8 writes a where a_s is meant. The text after Eq. 9 names P_o where
+    Eq. 11 defines P_c.
+  * LT is a radius (Sec. 1), so a_s, a_e are the mean LT radius.
+  * Mean LT is over all voxels of the object; the shell uses face neighbours
+    (4 in 2D, 6 in 3D); a neighbour outside the array or with another label
+    counts as outside the object.
+  * Objects are the voxels of one nonzero label; labels must be zero outside
+    the mask.
+
+Parity pins (tests/test_oracle_*.py): brute force on tiny inputs, scipy's
+exact EDT, digital balls and discs (known lattice counts), numeric
+quadrature of the spheroid surface, the complete elliptic integral for the
+ellipse perimeter, and the sphere/circle limits S = 1, R = 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lt_oracle.c")
+_SO = os.path.join(_HERE, "_lt_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C loops into oracle/_lt_oracle.so."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.oracle_dt2.argtypes = [vp, i64, i64, i64, i32, vp]
+        lib.oracle_dt2.restype = None
+        lib.oracle_dt2_at.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp]
+        lib.oracle_dt2_at.restype = None
+        lib.oracle_lt2.argtypes = [vp, vp, i64, i64, i64, i32, vp]
+        lib.oracle_lt2.restype = None
+        lib.oracle_objects.argtypes = [vp, i64, i64, i64, i32, vp, vp, i64, vp, vp]
+        lib.oracle_objects.restype = None
+        _lib = lib
+    return _lib
+
+
+def _dims(a: np.ndarray):
+    if a.ndim == 2:
+        return 2, a.shape[1], a.shape[0], 1
+    if a.ndim == 3:
+        return 3, a.shape[2], a.shape[1], a.shape[0]
+    raise ValueError("2D or 3D arrays only")
+
+
+# ----------------------------------------------------------------- DT and LT
+def dt2(mask: np.ndarray) -> np.ndarray:
+    """Squared EDT by the definition (nearest background, padded array)."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ndim, nx, ny, nz = _dims(mask)
+    out = np.empty(mask.shape, np.uint32)
+    _load().oracle_dt2(mask.ctypes.data, nx, ny, nz, ndim, out.ctypes.data)
+    return out
+
+
+def dt2_at(mask: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """DT2 at the given linear voxel indices."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    ndim, nx, ny, nz = _dims(mask)
+    out = np.empty(idx.shape, np.uint32)
+    _load().oracle_dt2_at(mask.ctypes.data, nx, ny, nz, ndim, idx.ctypes.data, idx.size,
+                          out.ctypes.data)
+    return out
+
+
+def lt2(dt2_arr: np.ndarray, labels: np.ndarray) -> np.ndarray:
+    """Squared local thickness by painting from every labelled centre."""
+    d = np.ascontiguousarray(dt2_arr, dtype=np.uint32)
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    ndim, nx, ny, nz = _dims(d)
+    out = np.empty(d.shape, np.uint32)
+    _load().oracle_lt2(d.ctypes.data, lab.ctypes.data, nx, ny, nz, ndim, out.ctypes.data)
+    return out
+
+
+def objects_dt2_lt2(mask: np.ndarray, labels: np.ndarray, which):
+    """DT2 and LT2 of the voxels of selected labels, one object at a time.
+
+    Returns {label: (linear_indices, dt2, lt2)}.
+    """
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ndim, nx, ny, nz = _dims(mask)
+    flat = labels.reshape(-1)
+    which = [int(w) for w in which]
+    sel = np.isin(flat, np.asarray(which, dtype=flat.dtype))
+    idx_all = np.flatnonzero(sel)
+    lab_all = flat[idx_all]
+    order = np.argsort(lab_all, kind="stable")
+    idx_all, lab_all = idx_all[order], lab_all[order]
+    bounds = np.searchsorted(lab_all, np.asarray(which, dtype=lab_all.dtype), side="left")
+    ends = np.searchsorted(lab_all, np.asarray(which, dtype=lab_all.dtype), side="right")
+    idx_list = [idx_all[b:e] for b, e in zip(bounds, ends)]
+    off = np.zeros(len(which) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in idx_list])
+    idx = np.ascontiguousarray(np.concatenate(idx_list) if idx_list else np.zeros(0, np.int64),
+                               dtype=np.int64)
+    d_out = np.empty(idx.shape, np.uint32)
+    l_out = np.empty(idx.shape, np.uint32)
+    _load().oracle_objects(mask.ctypes.data, nx, ny, nz, ndim, idx.ctypes.data, off.ctypes.data,
+                           len(which), d_out.ctypes.data, l_out.ctypes.data)
+    return {w: (idx[off[k]:off[k + 1]], d_out[off[k]:off[k + 1]], l_out[off[k]:off[k + 1]])
+            for k, w in enumerate(which)}
+
+
+def dt2_brute(mask: np.ndarray) -> np.ndarray:
+    """All-pairs DT2 for tiny arrays: every voxel against every background
+    voxel of the array padded by one background layer."""
+    m = np.pad(np.asarray(mask) != 0, 1, constant_values=False)
+    bg = np.argwhere(~m).astype(np.int64)
+    fg = np.argwhere(m).astype(np.int64)
+    out = np.zeros(m.shape, np.int64)
+    if len(fg):
+        d = ((fg[:, None, :] - bg[None, :, :]) ** 2).sum(-1).min(1)
+        out[tuple(fg.T)] = d
+    sl = tuple(slice(1, -1) for _ in range(m.ndim))
+    return out[sl].astype(np.uint32)
+
+
+def lt2_brute(dt2_arr: np.ndarray, labels: np.ndarray) -> np.ndarray:
+    """All-pairs local thickness for tiny arrays."""
+    d = np.asarray(dt2_arr).astype(np.int64)
+    lab = np.asarray(labels)
+    pts = np.argwhere(lab != 0).astype(np.int64)
+    out = np.zeros(d.shape, np.int64)
+    if len(pts):
+        r2 = d[tuple(pts.T)]
+        pl = lab[tuple(pts.T)]
+        dist2 = ((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)  # [target, centre]
+        ok = (dist2 <= r2[None, :]) & (pl[:, None] == pl[None, :])
+        out[tuple(pts.T)] = np.where(ok, r2[None, :], 0).max(1)
+    return out.astype(np.uint32)
+
+
+# ----------------------------------------------------------- per-object sums
+def shell_mask(labels: np.ndarray) -> np.ndarray:
+    """Object voxels with a face neighbour (4 in 2D, 6 in 3D) outside the
+    object: another label, background, or outside the array (Sec. 4.2)."""
+    lab = np.asarray(labels)
+    p = np.pad(lab, 1, constant_values=0)
+    core = tuple(slice(1, -1) for _ in range(lab.ndim))
+    shell = np.zeros(lab.shape, bool)
+    for ax in range(lab.ndim):
+        for s in (-1, 1):
+            sl = list(core)
+            sl[ax] = slice(1 + s, p.shape[ax] - 1 + s)
+            shell |= p[tuple(sl)] != lab
+    return shell & (lab != 0)
+
+
+def object_stats(labels: np.ndarray, lt2_arr: np.ndarray, n_labels: int) -> dict:
+    """FP64 per-label sums (label 0 is background and is reported as empty)."""
+    lab = np.asarray(labels).reshape(-1).astype(np.int64)
+    if lab.size and lab.max() >= n_labels:
+        raise ValueError("label >= n_labels")
+    lt = np.sqrt(np.asarray(lt2_arr).reshape(-1).astype(np.float64))
+    sh = shell_mask(labels).reshape(-1)
+    obj = lab != 0
+    V = np.bincount(lab[obj], minlength=n_labels).astype(np.int64)
+    ns = np.bincount(lab[sh], minlength=n_labels).astype(np.int64)
+    s_lt = np.bincount(lab[obj], weights=lt[obj], minlength=n_labels)
+    s_sh = np.bincount(lab[sh], weights=lt[sh], minlength=n_labels)
+    mx = np.zeros(n_labels, np.int64)
+    np.maximum.at(mx, lab[obj], np.asarray(lt2_arr).reshape(-1)[obj].astype(np.int64))
+    V[0] = ns[0] = mx[0] = 0
+    s_lt[0] = s_sh[0] = 0.0
+    return {"volume": V, "n_shell": ns, "sum_lt": s_lt, "sum_shell_lt": s_sh, "max_lt2": mx}
+
+
+# --------------------------------------------------------- shape formulas
+def spheroid_area(a: float, c: float) -> float:
+    """Surface area of a spheroid with equal semi-axes a and third semi-axis c
+    (Eqs. 6-7, with e the eccentricity, read with its square root)."""
+    if c == a:
+        return 4.0 * math.pi * a * a
+    if c < a:
+        e = math.sqrt(1.0 - (c * c) / (a * a))
+        return 2.0 * math.pi * a * a * (1.0 + (1.0 - e * e) / e * math.atanh(e))
+    e = math.sqrt(1.0 - (a * a) / (c * c))
+    return 2.0 * math.pi * a * a * (1.0 + c / (a * e) * math.asin(e))
+
+
+def ramanujan_perimeter(a: float, b: float) -> float:
+    """Ramanujan's first approximation of an ellipse perimeter (Eq. 9)."""
+    return math.pi * (3.0 * (a + b) - math.sqrt((3.0 * a + b) * (a + 3.0 * b)))
+
+
+def sphericity_3d(V: float, mean_lt: float) -> float:
+    """S_LT in 3D: Eq. 1 with the spheroid area of Eqs. 6-8."""
+    a = mean_lt
+    c = 3.0 * V / (4.0 * math.pi * a * a)
+    return math.pi ** (1.0 / 3.0) * (6.0 * V) ** (2.0 / 3.0) / spheroid_area(a, c)
+
+
+def sphericity_2d(A: float, mean_lt: float) -> float:
+    """S_LT in 2D: Eq. 2 with P_o from Eqs. 9-10 and P_c from Eq. 11."""
+    a = mean_lt
+    b = A / (math.pi * a)
+    return 2.0 * math.sqrt(math.pi * A) / ramanujan_perimeter(a, b)
+
+
+def roundness(sum_shell_lt: float, n_shell: int, max_lt2: int) -> float:
+    """R_LT: mean LT over the contour/surface divided by the largest LT (Sec. 4.2)."""
+    return (sum_shell_lt / n_shell) / math.sqrt(max_lt2)
+
+
+def measures(labels: np.ndarray, lt2_arr: np.ndarray, n_labels: int):
+    """(sphericity, roundness, stats) in FP64; NaN for labels with no voxel."""
+    st = object_stats(labels, lt2_arr, n_labels)
+    nd = np.asarray(labels).ndim
+    S = np.full(n_labels, np.nan)
+    R = np.full(n_labels, np.nan)
+    for l in range(1, n_labels):
+        V = int(st["volume"][l])
+        if V == 0:
+            continue
+        mean_lt = st["sum_lt"][l] / V
+        S[l] = sphericity_3d(V, mean_lt) if nd == 3 else sphericity_2d(V, mean_lt)
+        R[l] = roundness(st["sum_shell_lt"][l], int(st["n_shell"][l]), int(st["max_lt2"][l]))
+    return S, R, st
+
+
+def pipeline(mask: np.ndarray, labels: np.ndarray, n_labels: int):
+    """mask, labels -> (dt2, lt2, sphericity, roundness) by the oracle."""
+    lab = np.asarray(labels)
+    if np.any((lab != 0) & (np.asarray(mask) == 0)):
+        raise ValueError("labels must be zero outside the mask")
+    d = dt2(mask)
+    l2 = lt2(d, lab)
+    S, R, _ = measures(lab, l2, n_labels)
+    return d, l2, S, R
