@@ -1,0 +1,296 @@
+"""Benchmark: Mvoxels/s of the whole path (exact EDT -> exact local thickness
+-> per-object sphericity and roundness) on the 512^3 particle volume.
+
+One step = lt_measure over the resident volume (every kernel of the path).
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank processes
+its own volume (replicas, weak scaling); value = voxels of all ranks / max
+time over ranks.
+
+--impl reference times the CPU oracle (plain definition-level C loops) on a
+bounded slab of the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mvoxels/s EDT+LT+shape at 512^3"
+UNIT = "Mvoxels/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="particles_3d_512")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(name, n, n_surv):
+    """Bytes a kernel must move per launch by its definition."""
+    table = {
+        "edt_rows_x": 5 * n,          # mask in, g^2 out
+        "edt_cols_y": 8 * n,          # u32 in, u32 out
+        "edt_cols_z": 8 * n,
+        "lt_ridge": 12 * n + 8 * n_surv,  # DT2, labels in; LT2 cleared; centres out
+        "shape_reduce": 8 * n,        # labels, LT2 in
+    }
+    return table.get(name)
+
+
+def cpu_oracle_rate(mask, labels, n_labels, target_s=15.0):
+    """The oracle as it stands on a z-slab of the workload; slab grown until
+    one run takes about target_s seconds (bounded)."""
+    import oracle
+    oracle.build()
+    nz = mask.shape[0]
+    t = 8
+    while True:
+        sl = slice(0, min(t, nz))
+        m, l = np.ascontiguousarray(mask[sl]), np.ascontiguousarray(labels[sl])
+        t0 = time.perf_counter()
+        oracle.pipeline(m, l, n_labels)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 3 or t >= nz:
+            break
+        t = min(nz, max(t * 2, int(t * target_s / max(dt, 1e-3) / 2)))
+    return m.size / dt / 1e6, f"z-slab {m.shape[0]}x{m.shape[1]}x{m.shape[2]} of the workload", dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    mask, labels, n = synth.workload(args.workload, args.seed)
+    import oracle
+    oracle.build()
+    # size each step so that warmup + steps stay within about two minutes
+    per_step = max(0.5, min(5.0, 120.0 / max(1, args.steps + args.warmup)))
+    rate, sample, _ = cpu_oracle_rate(mask, labels, n, target_s=per_step * 3)
+    t = int(sample.split()[1].split("x")[0])
+    m, l = np.ascontiguousarray(mask[:t]), np.ascontiguousarray(labels[:t])
+    for _ in range(args.warmup):
+        oracle.pipeline(m, l, n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pipeline(m, l, n)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = m.size / dt / 1e6
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+           "data": "synthetic", "config": {"workload": args.workload, "seed": args.seed,
+                                           "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import synth
+    import paper_2504_05808_gb300 as lt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    mask, labels, n_labels = synth.workload(args.workload, args.seed + rank)
+    nd = mask.ndim
+    shape = mask.shape
+    nvox = mask.size
+    dev = torch.device("cuda", local)
+    m = torch.from_numpy(mask).to(dev)
+    l = torch.from_numpy(labels.view(np.int32)).to(dev)
+    dt2 = torch.empty(shape, dtype=torch.int32, device=dev)
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n_labels, dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    nz, ny, nx = (1,) + shape if nd == 2 else shape
+    ws = lt.workspace(lt.lib.lt_measure_workspace_size(n_labels, nd, nx, ny, nz), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(3, args.warmup)):
+        lt.lt_measure(m, l, n_labels, dt2, lt2, S, R, ws=ws)
+    lt.lt_workspace_status(ws)
+    n_surv = int(ws[8:12].view(torch.int32).item())
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    lt.lt_trace_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lt.lt_measure(m, l, n_labels, dt2, lt2, S, R, ws=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    lt.lt_trace_enable(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    trace = lt.lt_trace_summary()
+    lt.lt_workspace_status(ws)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nvox / (ms * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    mh = torch.from_numpy(mask).pin_memory()
+    lh = torch.from_numpy(labels.view(np.int32)).pin_memory()
+    Sh = torch.empty(n_labels, dtype=torch.float32).pin_memory()
+    Rh = torch.empty(n_labels, dtype=torch.float32).pin_memory()
+    del ws
+    wsh = lt.workspace(lt.lt_measure_host_workspace_size(n_labels, shape), dev)
+    for _ in range(2):
+        lt.lt_measure_host(mh, lh, n_labels, Sh, Rh, wsh)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        lt.lt_measure_host(mh, lh, n_labels, Sh, Rh, wsh)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * nvox / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(mask.nbytes + labels.nbytes),
+           "d2h_bytes_per_step": int(2 * 4 * n_labels)}
+
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0]),
+                   "share": v[1] / max(1e-9, sum(x[1] for x in trace.values()))}
+               for k, v in trace.items()}
+    dom = max(trace, key=lambda k: trace[k][1])
+    avg_ms = trace[dom][1] / trace[dom][0]
+    ab = algorithmic_bytes(dom, nvox, n_surv)
+    roof = {"kernel": dom, "bound": "hbm", "peak": peak, "unit": "GB/s",
+            "peak_source": peak_kind, "traffic": None,
+            "avg_ms": avg_ms, "achieved": None, "frac": None}
+    if ab is not None:
+        roof["achieved"] = ab / (avg_ms * 1e-3) / 1e9
+        roof["frac"] = roof["achieved"] / peak
+        roof["algorithmic_bytes"] = ab
+    gpu_launches = sum(v[0] for v in trace.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, _ = cpu_oracle_rate(mask, labels, n_labels)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+               "data": "synthetic",
+               "config": {"workload": args.workload, "voxels": nvox, "objects": n_labels - 1,
+                          "foreground": float(mask.mean()), "centres_kept": n_surv,
+                          "seed": args.seed, "parallelism": f"replicas{world}",
+                          "l2": "inputs larger than L2 (no flush needed)"},
+               "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": gpu_launches, "clocks": clk}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

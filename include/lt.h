@@ -1,0 +1,191 @@
+/*
+ * lt.h — C ABI of the GB300 (sm_103a) local-thickness shape library.
+ *
+ * Method: "Fast Sphericity and Roundness approximation in 2D and 3D using
+ * Local Thickness" (Pieta, Rasmussen, Dahl, Christensen). A labelled mask
+ * goes through
+ *     lt_edt              exact squared Euclidean distance transform,
+ *     lt_local_thickness  exact local thickness (squared radius),
+ *     lt_shape_measures   per-object sphericity S_LT and roundness R_LT,
+ * each a sequence of hand-written CUDA kernels. lt_measure runs all three.
+ *
+ * Conventions shared by every call
+ *   Layout      C order [z][y][x], x fastest. ndim = 2 requires nz = 1 and
+ *               treats the array as an (ny, nx) image; ndim = 3 is a volume.
+ *   Limits      1 <= nx, ny, nz <= 8192 and nx * ny * nz < 2^32, so that
+ *               every squared distance is below 2^24 and every voxel index
+ *               fits in 32 bits. Violations return LT_ERR_DIMS.
+ *   Pointers    Device pointers unless the name ends in _host. Device buffers
+ *               are owned by the caller and must be 16-byte aligned.
+ *   Workspace   Scratch memory is always passed in by the caller (`ws`,
+ *               `ws_bytes`, 256-byte aligned); the library allocates nothing.
+ *               Size it with the matching *_workspace_size function. A
+ *               workspace may be reused across calls on the same stream;
+ *               concurrent calls need distinct workspaces.
+ *   Streams     `stream` is a cudaStream_t (NULL = the legacy default
+ *               stream). Device-pointer calls only enqueue work and return;
+ *               argument errors are returned immediately and nothing is
+ *               enqueued. Errors that only the device can see (a label out of
+ *               range, a labelled voxel outside the mask) are recorded in the
+ *               workspace; read them with lt_workspace_status.
+ *   Threads     Calls are thread-safe as long as they use distinct
+ *               workspaces and outputs.
+ *
+ * Definitions (the paper's Sec. 1 and Sec. 4)
+ *   Foreground  mask != 0. Everything outside the array counts as background
+ *               (the array is padded by one background layer).
+ *   DT2(p)      min |p - b|^2 over background b; 0 on background.
+ *   Object l    the voxels with label l != 0. Labels must be 0 wherever the
+ *               mask is 0 (checked on the device). Foreground voxels with
+ *               label 0 shape the distance transform but belong to no object.
+ *   LT2(x)      the local thickness squared: the largest DT2(c) over centres
+ *               c of x's object whose inclusive ball |x - c|^2 <= DT2(c)
+ *               holds x (local thickness = radius of the largest inscribed
+ *               ball containing x); 0 outside every object.
+ *   Shell       object voxels with a face neighbour (4 in 2D, 6 in 3D)
+ *               outside the object: another label, background, or outside
+ *               the array (Sec. 4.2).
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lt_status {
+  LT_OK = 0,
+  LT_ERR_INVALID_ARG = 1,         /* null or misaligned pointer, bad ndim */
+  LT_ERR_DIMS = 2,                /* dimensions outside the limits above */
+  LT_ERR_WORKSPACE = 3,           /* workspace missing, too small or misaligned */
+  LT_ERR_LABEL_RANGE = 4,         /* device-detected: a label >= n_labels */
+  LT_ERR_LABEL_OUTSIDE_MASK = 5,  /* device-detected: label != 0 where mask == 0 */
+  LT_ERR_CUDA = 6,                /* a CUDA call or kernel launch failed */
+  LT_ERR_NO_DEVICE = 7            /* no usable sm_103 device */
+} lt_status;
+
+/* Per-object sums, one entry per label (structure of arrays, device memory).
+ * sum_lt and sum_shell_lt are fixed point: the sum over voxels of
+ * round(sqrtf(LT2) * 2^20), sqrtf the IEEE single-precision square root (so
+ * each term is within 2^-24 relative plus 2^-21 absolute of the exact LT
+ * times 2^20; the sums are exact integers, independent of summation order). */
+typedef struct lt_object_stats {
+  uint32_t* volume;        /* voxel (pixel) count V (area A in 2D) */
+  uint32_t* n_shell;       /* shell voxel count */
+  uint32_t* max_lt2;       /* largest LT2 of the object (= largest DT2) */
+  uint64_t* sum_lt;        /* fixed point, scale 2^20 */
+  uint64_t* sum_shell_lt;  /* fixed point, scale 2^20 */
+} lt_object_stats;
+
+#define LT_FIXED_POINT_SHIFT 20
+
+/* Short English name of a status code (static storage). */
+const char* lt_status_string(lt_status status);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+uint32_t lt_version(void);
+
+/* ------------------------------------------------------------------ EDT --
+ * Exact squared Euclidean distance transform of `mask` (uint8, nonzero =
+ * foreground) into `dt2` (uint32, DT2 as defined above; 0 on background).
+ * Three separable passes: a row pass along x (distance to the nearest
+ * background in the row, exact integer), then the lower envelope of the
+ * parabolas f(q) + (p - q)^2 along y and (3D) along z, with the padding
+ * layer entering as two zero-height parabolas at -1 and n. All arithmetic is
+ * exact integer arithmetic, so the result is bit-exact.
+ * Workspace: lt_edt_workspace_size bytes (0 for every axis length up to
+ * 2048, where the strided passes run fully in shared memory; otherwise one
+ * uint32 per voxel). `ws` may be NULL when the size is 0. */
+size_t lt_edt_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64_t ny, int64_t nz,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------- local thickness --
+ * Exact local thickness squared, LT2 as defined above, from `dt2` (output of
+ * lt_edt) and `labels` (uint32) into `lt2` (uint32). Bit-exact.
+ * Centres whose ball lies inside a same-label neighbour's ball of larger
+ * radius are dropped (an exact digital-ball containment test by lookup
+ * table); every other centre raises LT2 (atomic max) only on the voxels of
+ * its ball that one chosen higher-ranked neighbour's ball does not hold.
+ * Neither step changes the maximum (proof in the kernel source).
+ * Device-detected error: LT_ERR_LABEL_OUTSIDE_MASK.
+ * Workspace: lt_local_thickness_workspace_size bytes (8 bytes per voxel for
+ * the centre list plus a lookup table of at most 3 MiB). */
+size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, int ndim,
+                             int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* --------------------------------------------------------- shape measures --
+ * Per-object sphericity and roundness from `labels` and `lt2` (as produced by
+ * lt_local_thickness) for labels 0 .. n_labels-1.
+ *   3D (Eqs. 1, 6-8): a = mean LT over the object, c = 3V / (4 pi a^2);
+ *      spheroid area with e = sqrt(1 - c^2/a^2) (c < a) or
+ *      e = sqrt(1 - a^2/c^2) (c > a), 4 pi a^2 at c = a;
+ *      S = pi^(1/3) (6V)^(2/3) / area.
+ *   2D (Eqs. 2, 9-11): a = mean LT, b = A / (pi a), Ramanujan's
+ *      P_o = pi (3(a + b) - sqrt((3a + b)(a + 3b))), P_c = 2 sqrt(pi A),
+ *      S = P_c / P_o.
+ *   R (Sec. 4.2) = (mean LT over the shell) / sqrt(max LT2).
+ * Outputs `sphericity[n_labels]`, `roundness[n_labels]` (float, device; NaN
+ * for label 0 and for labels with no voxel); either may be NULL. `stats` may
+ * be NULL; when given, its arrays (device, n_labels entries each) receive the
+ * per-object sums. The sums are exact integers and the formulas run in FP64;
+ * the result is within 1e-6 relative of an FP64 evaluation with exact sums.
+ * Device-detected error: LT_ERR_LABEL_RANGE (such voxels are skipped).
+ * Workspace: lt_shape_workspace_size bytes (28 bytes per label + 256). */
+size_t lt_shape_workspace_size(uint32_t n_labels);
+lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, int ndim,
+                            int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                            float* sphericity, float* roundness, const lt_object_stats* stats,
+                            void* stream);
+
+/* ------------------------------------------------------------- pipeline --
+ * lt_edt, lt_local_thickness and lt_shape_measures in sequence on one
+ * workspace. dt2 and lt2 are outputs (device, one uint32 per voxel each). */
+size_t lt_measure_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, int ndim,
+                     int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2,
+                     uint32_t* lt2, float* sphericity, float* roundness, void* stream);
+
+/* Host-buffer form of lt_measure for callers whose data lives in host memory:
+ * copies mask_host and labels_host to the device, runs the pipeline, copies
+ * sphericity_host and roundness_host (n_labels floats each) back and waits
+ * for the stream. Host buffers should be pinned for full copy speed. The
+ * device copies of the inputs, DT2 and LT2 live in `ws` (device memory,
+ * lt_measure_host_workspace_size bytes). Returns device-detected errors too. */
+size_t lt_measure_host_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host, uint32_t n_labels,
+                          int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                          float* sphericity_host, float* roundness_host, void* stream);
+
+/* ------------------------------------------------------------- tracing --
+ * Kernel timing for profiling. While tracing is enabled, the library records
+ * a CUDA event on the launch stream before and after every kernel it
+ * launches (events come from a pool created on first use, so tracing can
+ * stay on inside timed loops). lt_trace_enable(1) clears earlier records;
+ * lt_trace_enable(0) stops recording. lt_trace_summary waits for the
+ * recorded events, then writes up to max_entries per-kernel totals (name,
+ * launches, summed event time in ms) and returns the number of distinct
+ * kernels seen (negative on a CUDA error). Not meant for use while a stream
+ * is being captured into a CUDA graph. */
+typedef struct lt_trace_entry {
+  char name[40];
+  uint32_t launches;
+  double total_ms;
+} lt_trace_entry;
+lt_status lt_trace_enable(int enable);
+int lt_trace_summary(lt_trace_entry* out, int max_entries);
+
+/* Waits for `stream`, then returns the first device-detected error recorded
+ * in `ws` since the last call that used it (LT_OK if none). */
+lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LT_H */

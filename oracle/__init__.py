@@ -269,6 +269,31 @@ def measures(labels: np.ndarray, lt2_arr: np.ndarray, n_labels: int):
     return S, R, st
 
 
+def object_measures_from_voxels(labels: np.ndarray, idx: np.ndarray, lt2_vals: np.ndarray):
+    """S and R of one object given its voxels (linear indices into labels)
+    and their LT2, for objects of arrays too large to process whole. The
+    shell test looks at the object's face neighbours in `labels`."""
+    lab = np.asarray(labels)
+    shape = lab.shape
+    flat = lab.reshape(-1)
+    l = flat[idx[0]]
+    coords = np.unravel_index(idx, shape)
+    shell = np.zeros(idx.shape, bool)
+    for ax in range(lab.ndim):
+        for s in (-1, 1):
+            c = list(coords)
+            c[ax] = c[ax] + s
+            out = (c[ax] < 0) | (c[ax] >= shape[ax])
+            c[ax] = np.clip(c[ax], 0, shape[ax] - 1)
+            shell |= out | (flat[np.ravel_multi_index(tuple(c), shape)] != l)
+    lt = np.sqrt(np.asarray(lt2_vals).astype(np.float64))
+    V = idx.size
+    mean_lt = lt.sum() / V
+    S = sphericity_3d(V, mean_lt) if lab.ndim == 3 else sphericity_2d(V, mean_lt)
+    R = roundness(lt[shell].sum(), int(shell.sum()), int(np.max(lt2_vals)))
+    return S, R
+
+
 def pipeline(mask: np.ndarray, labels: np.ndarray, n_labels: int):
     """mask, labels -> (dt2, lt2, sphericity, roundness) by the oracle."""
     lab = np.asarray(labels)

@@ -1,0 +1,196 @@
+"""Python binding of the GB300 local-thickness shape library (include/lt.h).
+
+Argument marshalling only: every step runs in the CUDA kernels of _lt.so.
+PyTorch provides device memory and streams. There is no CPU fallback: if the
+library has not been built (python -c "import __graft_entry__ as g; g.build()")
+importing this package raises ImportError.
+
+Tensors: mask uint8; labels, dt2, lt2 int32 or uint32 (bit patterns are
+reinterpreted as uint32); shape (ny, nx) for 2D or (nz, ny, nx) for 3D,
+contiguous, on a CUDA device. Calls run on torch's current stream unless a
+stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lt.so")
+
+LT_OK = 0
+STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_DIMS", 3: "LT_ERR_WORKSPACE",
+                4: "LT_ERR_LABEL_RANGE", 5: "LT_ERR_LABEL_OUTSIDE_MASK", 6: "LT_ERR_CUDA",
+                7: "LT_ERR_NO_DEVICE"}
+FIXED_POINT_SHIFT = 20
+
+# exported symbol -> (restype, argtypes)
+_vp, _sz, _i32, _i64, _u32 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int64,
+                             ctypes.c_uint32)
+_DIMS = [_i32, _i64, _i64, _i64]
+SIGNATURES = {
+    "lt_status_string": (ctypes.c_char_p, [_i32]),
+    "lt_version": (_u32, []),
+    "lt_edt_workspace_size": (_sz, _DIMS),
+    "lt_edt": (_i32, [_vp, _vp] + _DIMS + [_vp, _sz, _vp]),
+    "lt_local_thickness_workspace_size": (_sz, _DIMS),
+    "lt_local_thickness": (_i32, [_vp, _vp, _vp] + _DIMS + [_vp, _sz, _vp]),
+    "lt_shape_workspace_size": (_sz, [_u32]),
+    "lt_shape_measures": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp]),
+    "lt_measure_workspace_size": (_sz, [_u32] + _DIMS),
+    "lt_measure": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
+    "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
+    "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
+    "lt_trace_enable": (_i32, [_i32]),
+    "lt_trace_summary": (_i32, [_vp, _i32]),
+}
+
+
+class LTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class ObjectStats(ctypes.Structure):
+    _fields_ = [("volume", _vp), ("n_shell", _vp), ("max_lt2", _vp), ("sum_lt", _vp),
+                ("sum_shell_lt", _vp)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing; build it with "
+                          "python paper_2504_05808_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, where: str):
+    if status != LT_OK:
+        raise LTError(status, where)
+
+
+def _dims(t):
+    if t.dim() == 2:
+        return 2, t.shape[1], t.shape[0], 1
+    if t.dim() == 3:
+        return 3, t.shape[2], t.shape[1], t.shape[0]
+    raise ValueError("expected a 2D or 3D tensor")
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def workspace(nbytes: int, device):
+    """Device workspace (uint8 tensor; torch's allocator aligns to 512 bytes)."""
+    import torch
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def lt_edt(mask, dt2, ws=None, stream=None):
+    nd, nx, ny, nz = _dims(mask)
+    need = lib.lt_edt_workspace_size(nd, nx, ny, nz)
+    if need and ws is None:
+        ws = workspace(need, mask.device)
+    _check(lib.lt_edt(_ptr(mask), _ptr(dt2), nd, nx, ny, nz, _ptr(ws) if need else None,
+                      ws.numel() if need else 0, _stream(stream)), "lt_edt")
+
+
+def lt_local_thickness(dt2, labels, lt2, ws=None, stream=None):
+    nd, nx, ny, nz = _dims(dt2)
+    if ws is None:
+        ws = workspace(lib.lt_local_thickness_workspace_size(nd, nx, ny, nz), dt2.device)
+    _check(lib.lt_local_thickness(_ptr(dt2), _ptr(labels), _ptr(lt2), nd, nx, ny, nz, _ptr(ws),
+                                  ws.numel(), _stream(stream)), "lt_local_thickness")
+    return ws
+
+
+def lt_shape_measures(labels, lt2, n_labels, sphericity=None, roundness=None, stats=None,
+                      ws=None, stream=None):
+    """stats: optional dict of device tensors volume, n_shell, max_lt2 (int32,
+    n_labels) and sum_lt, sum_shell_lt (int64, n_labels)."""
+    nd, nx, ny, nz = _dims(labels)
+    if ws is None:
+        ws = workspace(lib.lt_shape_workspace_size(n_labels), labels.device)
+    st = None
+    if stats is not None:
+        st = ObjectStats(*[stats[k].data_ptr() if k in stats else None
+                           for k in ("volume", "n_shell", "max_lt2", "sum_lt", "sum_shell_lt")])
+    _check(lib.lt_shape_measures(_ptr(labels), _ptr(lt2), n_labels, nd, nx, ny, nz, _ptr(ws),
+                                 ws.numel(), _ptr(sphericity), _ptr(roundness),
+                                 ctypes.byref(st) if st is not None else None, _stream(stream)),
+           "lt_shape_measures")
+    return ws
+
+
+def lt_measure(mask, labels, n_labels, dt2, lt2, sphericity, roundness, ws=None, stream=None):
+    nd, nx, ny, nz = _dims(mask)
+    if ws is None:
+        ws = workspace(lib.lt_measure_workspace_size(n_labels, nd, nx, ny, nz), mask.device)
+    _check(lib.lt_measure(_ptr(mask), _ptr(labels), n_labels, nd, nx, ny, nz, _ptr(ws), ws.numel(),
+                          _ptr(dt2), _ptr(lt2), _ptr(sphericity), _ptr(roundness),
+                          _stream(stream)), "lt_measure")
+    return ws
+
+
+def lt_measure_host(mask_host, labels_host, n_labels, sphericity_host, roundness_host, ws,
+                    stream=None):
+    """Host tensors (ideally pinned) in and out; ws is a device workspace of
+    lt_measure_host_workspace_size bytes. Synchronises the stream."""
+    nd, nx, ny, nz = _dims(mask_host)
+    for t in (mask_host, labels_host, sphericity_host, roundness_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected contiguous host tensors")
+    _check(lib.lt_measure_host(ctypes.c_void_p(mask_host.data_ptr()),
+                               ctypes.c_void_p(labels_host.data_ptr()), n_labels, nd, nx, ny, nz,
+                               _ptr(ws), ws.numel(), ctypes.c_void_p(sphericity_host.data_ptr()),
+                               ctypes.c_void_p(roundness_host.data_ptr()), _stream(stream)),
+           "lt_measure_host")
+
+
+def lt_measure_host_workspace_size(n_labels, shape):
+    nd = len(shape)
+    nz, ny, nx = (1,) + tuple(shape) if nd == 2 else tuple(shape)
+    return lib.lt_measure_host_workspace_size(n_labels, nd, nx, ny, nz)
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", _u32), ("total_ms", ctypes.c_double)]
+
+
+def lt_trace_enable(enable: bool = True):
+    _check(lib.lt_trace_enable(1 if enable else 0), "lt_trace_enable")
+
+
+def lt_trace_summary():
+    """{kernel name: (launches, total ms)} of the kernels launched while
+    tracing was enabled (waits for their events)."""
+    buf = (TraceEntry * 64)()
+    n = lib.lt_trace_summary(buf, 64)
+    if n < 0:
+        raise LTError(6, "lt_trace_summary")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(min(n, 64))}
+
+
+def lt_workspace_status(ws, stream=None):
+    _check(lib.lt_workspace_status(_ptr(ws), ws.numel(), _stream(stream)), "device status")

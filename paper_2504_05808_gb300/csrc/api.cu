@@ -1,0 +1,378 @@
+// Host side of the C ABI declared in include/lt.h: argument checks, workspace
+// layout, device selection and the launch sequence. All compute is in the
+// kernels of edt.cu, lt.cu and shape.cu.
+#include <cstring>
+
+#include "lt_internal.cuh"
+
+using namespace ltk;
+
+namespace ltk {
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+cudaError_t allow_smem(const void* func, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  // Cheap and idempotent; called before each launch that needs more than
+  // the default 48 KiB.
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace ltk
+
+namespace {
+
+constexpr int kMaxAxis = 8192;
+
+lt_status make_dims(int ndim, int64_t nx, int64_t ny, int64_t nz, Dims* d) {
+  if (ndim != 2 && ndim != 3) return LT_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxAxis || ny > kMaxAxis || nz > kMaxAxis) return LT_ERR_DIMS;
+  if (ndim == 2 && nz != 1) return LT_ERR_DIMS;
+  const uint64_t n = (uint64_t)nx * (uint64_t)ny * (uint64_t)nz;
+  if (n >= (1ull << 32)) return LT_ERR_DIMS;
+  d->ndim = ndim;
+  d->nx = (int)nx;
+  d->ny = (int)ny;
+  d->nz = (int)nz;
+  d->n = (uint32_t)n;
+  return LT_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Makes the device that owns `p` current; rejects pointers the GPU cannot
+// address as device memory.
+lt_status use_device_of(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return LT_ERR_INVALID_ARG;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return LT_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return LT_ERR_CUDA;
+  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return LT_ERR_CUDA;
+  return LT_OK;
+}
+
+lt_status dev_ptr(const void* p) {
+  if (!p || !aligned(p, 16)) return LT_ERR_INVALID_ARG;
+  return use_device_of(p);
+}
+
+lt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LT_OK : LT_ERR_CUDA; }
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+lt_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return LT_OK;
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return LT_ERR_WORKSPACE;
+  return use_device_of(ws);
+}
+
+size_t measure_body_bytes(const Dims& d, uint32_t n_labels) {
+  size_t b = edt_workspace_bytes(d);
+  b = b > lt_workspace_bytes(d) ? b : lt_workspace_bytes(d);
+  const size_t sb = shape_workspace_bytes(n_labels);
+  return b > sb ? b : sb;
+}
+
+lt_status run_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
+                      void* ws, uint32_t* dt2, uint32_t* lt2, float* S, float* R, cudaStream_t s) {
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(body), s);
+  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s);
+  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lt_status_string(lt_status status) {
+  switch (status) {
+    case LT_OK: return "ok";
+    case LT_ERR_INVALID_ARG: return "invalid argument (null, misaligned or non-device pointer, or bad ndim)";
+    case LT_ERR_DIMS: return "dimensions outside the supported range";
+    case LT_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case LT_ERR_LABEL_RANGE: return "a label is >= n_labels";
+    case LT_ERR_LABEL_OUTSIDE_MASK: return "a voxel outside the mask carries a nonzero label";
+    case LT_ERR_CUDA: return "CUDA error";
+    case LT_ERR_NO_DEVICE: return "no usable CUDA device";
+  }
+  return "unknown status";
+}
+
+uint32_t lt_version(void) { return 0x000100u; }
+
+size_t lt_edt_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  return edt_workspace_bytes(d);
+}
+
+lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64_t ny, int64_t nz,
+                 void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(dt2)) != LT_OK) return st;
+  const size_t need = edt_workspace_bytes(d);
+  if ((st = check_ws(ws, ws_bytes, need)) != LT_OK) return st;
+  return cuda_status(edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(ws), as_stream(stream)));
+}
+
+size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  return sizeof(WsHeader) + lt_workspace_bytes(d);
+}
+
+lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, int ndim,
+                             int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                             void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if ((st = dev_ptr(dt2)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK)
+    return st;
+  if ((st = check_ws(ws, ws_bytes, sizeof(WsHeader) + lt_workspace_bytes(d))) != LT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, hdr + 1, s);
+  return cuda_status(e);
+}
+
+size_t lt_shape_workspace_size(uint32_t n_labels) {
+  return sizeof(WsHeader) + shape_workspace_bytes(n_labels);
+}
+
+lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, int ndim,
+                            int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                            float* sphericity, float* roundness, const lt_object_stats* stats,
+                            void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if (n_labels == 0) return LT_ERR_INVALID_ARG;
+  if ((st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK) return st;
+  if (sphericity && (st = dev_ptr(sphericity)) != LT_OK) return st;
+  if (roundness && (st = dev_ptr(roundness)) != LT_OK) return st;
+  if (stats) {
+    const void* arr[5] = {stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt, stats->sum_shell_lt};
+    for (const void* p : arr)
+      if (p && (st = dev_ptr(p)) != LT_OK) return st;
+  }
+  if ((st = check_ws(ws, ws_bytes, lt_shape_workspace_size(n_labels))) != LT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, hdr + 1, sphericity, roundness, stats, s);
+  return cuda_status(e);
+}
+
+size_t lt_measure_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  return sizeof(WsHeader) + measure_body_bytes(d, n_labels);
+}
+
+lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, int ndim,
+                     int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2,
+                     uint32_t* lt2, float* sphericity, float* roundness, void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if (n_labels == 0) return LT_ERR_INVALID_ARG;
+  if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(dt2)) != LT_OK ||
+      (st = dev_ptr(lt2)) != LT_OK)
+    return st;
+  if (sphericity && (st = dev_ptr(sphericity)) != LT_OK) return st;
+  if (roundness && (st = dev_ptr(roundness)) != LT_OK) return st;
+  if ((st = check_ws(ws, ws_bytes, sizeof(WsHeader) + measure_body_bytes(d, n_labels))) != LT_OK) return st;
+  return run_measure(mask, labels, n_labels, d, ws, dt2, lt2, sphericity, roundness, as_stream(stream));
+}
+
+static size_t host_layout(const Dims& d, uint32_t n_labels, size_t off[6]) {
+  size_t p = sizeof(WsHeader) + measure_body_bytes(d, n_labels);
+  p = align_up(p);
+  off[0] = p; p += align_up((size_t)d.n);                  // mask
+  off[1] = p; p += align_up((size_t)d.n * 4);              // labels
+  off[2] = p; p += align_up((size_t)d.n * 4);              // dt2
+  off[3] = p; p += align_up((size_t)d.n * 4);              // lt2
+  off[4] = p; p += align_up((size_t)n_labels * 4);         // sphericity
+  off[5] = p; p += align_up((size_t)n_labels * 4);         // roundness
+  return p;
+}
+
+size_t lt_measure_host_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  size_t off[6];
+  return host_layout(d, n_labels, off);
+}
+
+lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host, uint32_t n_labels,
+                          int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                          float* sphericity_host, float* roundness_host, void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if (n_labels == 0 || !mask_host || !labels_host || !sphericity_host || !roundness_host)
+    return LT_ERR_INVALID_ARG;
+  size_t off[6];
+  const size_t need = host_layout(d, n_labels, off);
+  if ((st = check_ws(ws, ws_bytes, need)) != LT_OK) return st;
+  char* base = reinterpret_cast<char*>(ws);
+  uint8_t* mask = reinterpret_cast<uint8_t*>(base + off[0]);
+  uint32_t* labels = reinterpret_cast<uint32_t*>(base + off[1]);
+  uint32_t* dt2 = reinterpret_cast<uint32_t*>(base + off[2]);
+  uint32_t* lt2 = reinterpret_cast<uint32_t*>(base + off[3]);
+  float* S = reinterpret_cast<float*>(base + off[4]);
+  float* R = reinterpret_cast<float*>(base + off[5]);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(mask, mask_host, (size_t)d.n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(labels, labels_host, (size_t)d.n * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return LT_ERR_CUDA;
+  st = run_measure(mask, labels, n_labels, d, ws, dt2, lt2, S, R, s);
+  if (st != LT_OK) return st;
+  e = cudaMemcpyAsync(sphericity_host, S, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(roundness_host, R, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return LT_ERR_CUDA;
+  return lt_workspace_status(ws, ws_bytes, stream);
+}
+
+lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ws_bytes < sizeof(WsHeader) || !aligned(ws, kAlign)) return LT_ERR_WORKSPACE;
+  lt_status st = use_device_of(ws);
+  if (st != LT_OK) return st;
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
+  uint32_t err = 0;
+  if (cudaMemcpy(&err, ws, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return LT_ERR_CUDA;
+  if (err & ERR_LABEL_OUTSIDE_MASK) return LT_ERR_LABEL_OUTSIDE_MASK;
+  if (err & ERR_LABEL_RANGE) return LT_ERR_LABEL_RANGE;
+  return LT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ tracing
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace {
+
+struct TraceRecord {
+  std::string name;
+  cudaEvent_t start, stop;
+  int device;
+};
+
+struct TraceState {
+  std::mutex mu;
+  bool enabled = false;
+  std::vector<TraceRecord> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;  // free event pairs
+  std::vector<std::pair<std::string, std::pair<uint32_t, double>>> totals;
+};
+
+TraceState& trace() {
+  static TraceState* t = new TraceState();  // never destroyed: events may outlive static teardown
+  return *t;
+}
+
+}  // namespace
+
+namespace ltk {
+
+TraceScope::TraceScope(const char* name, cudaStream_t s) : slot_(-1), s_(s) {
+  TraceState& t = trace();
+  std::lock_guard<std::mutex> g(t.mu);
+  if (!t.enabled) return;
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (!t.pool.empty()) {
+    ev = t.pool.back();
+    t.pool.pop_back();
+  } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaEventRecord(ev.first, s);
+  t.pending.push_back({name, ev.first, ev.second, dev});
+  slot_ = (int)t.pending.size() - 1;
+}
+
+TraceScope::~TraceScope() {
+  if (slot_ < 0) return;
+  TraceState& t = trace();
+  std::lock_guard<std::mutex> g(t.mu);
+  if (slot_ < (int)t.pending.size()) cudaEventRecord(t.pending[slot_].stop, s_);
+}
+
+}  // namespace ltk
+
+extern "C" {
+
+lt_status lt_trace_enable(int enable) {
+  TraceState& t = trace();
+  std::lock_guard<std::mutex> g(t.mu);
+  if (enable) {
+    for (auto& r : t.pending) t.pool.push_back({r.start, r.stop});
+    t.pending.clear();
+    t.totals.clear();
+  }
+  t.enabled = enable != 0;
+  return LT_OK;
+}
+
+int lt_trace_summary(lt_trace_entry* out, int max_entries) {
+  TraceState& t = trace();
+  std::lock_guard<std::mutex> g(t.mu);
+  int bad = 0;
+  for (auto& r : t.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&ms, r.start, r.stop) != cudaSuccess) {
+      cudaGetLastError();
+      bad = 1;
+    }
+    bool found = false;
+    for (auto& e : t.totals)
+      if (e.first == r.name) {
+        e.second.first += 1;
+        e.second.second += ms;
+        found = true;
+        break;
+      }
+    if (!found) t.totals.push_back({r.name, {1u, (double)ms}});
+    t.pool.push_back({r.start, r.stop});
+  }
+  t.pending.clear();
+  if (bad) return -1;
+  const int n = (int)t.totals.size();
+  for (int i = 0; i < n && i < max_entries && out; ++i) {
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, t.totals[i].first.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = t.totals[i].second.first;
+    out[i].total_ms = t.totals[i].second.second;
+  }
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// Exact squared Euclidean distance transform on sm_103a.
+//
+// Separable form of DT2(p) = min over background b of |p - b|^2 with the
+// array padded by one background layer:
+//   pass x:  g(p)  = distance along the row to the nearest background voxel
+//                    (positions -1 and nx count as background); out = g^2.
+//   pass y:  f(p)  = min_q g^2(x, q, z) + (y - q)^2, plus the two padding
+//                    rows at y = -1 and y = ny (height 0).
+//   pass z:  same along z on f, giving DT2.
+// Every value is an exact integer below 2^24 (axis lengths <= 8192).
+//
+// The strided passes compute the lower envelope of the parabolas
+// q -> f(q) + (p - q)^2 at every p by scanning outwards from p and stopping
+// once k^2 reaches the best value found (no parabola at distance >= k can be
+// lower). Each CTA holds a full column tile (TX adjacent columns times the
+// whole axis) in shared memory, so the pass runs in place and is exact.
+#include "lt_internal.cuh"
+
+namespace ltk {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSeg = 512;       // voxels of a row handled by one warp step
+constexpr int kBig = 1 << 30;
+
+// Bit j set when voxel x0 + j (0 <= j < 16, x0 + j < nx) is background.
+template <bool VEC>
+__device__ __forceinline__ uint32_t zero_bits(const uint8_t* __restrict__ row, int x0, int nx) {
+  uint32_t bits = 0;
+  if (VEC && x0 + 16 <= nx) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + x0));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t m = __vcmpeq4(w[k], 0u) & 0x01010101u;
+      const uint32_t b = (m & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u);
+      bits |= b << (4 * k);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (x0 + j < nx && row[x0 + j] == 0) bits |= 1u << j;
+  }
+  return bits;
+}
+
+// One warp per row. Output: g^2 per voxel (0 on background).
+template <bool VEC>
+__global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict__ mask,
+                                                       uint32_t* __restrict__ out, int nx,
+                                                       uint32_t nrows) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t row = blockIdx.x * 8u + (threadIdx.x >> 5);
+  if (row >= nrows) return;  // uniform per warp
+  const uint8_t* mrow = mask + (size_t)row * nx;
+  uint32_t* orow = out + (size_t)row * nx;
+  const int nseg = (nx + kSeg - 1) / kSeg;  // <= 16
+
+  // First background position of each segment, held by lane == segment.
+  int segfirst = kBig;
+  for (int s = 0; s < nseg; ++s) {
+    const int x0 = s * kSeg + lane * 16;
+    const uint32_t z = zero_bits<VEC>(mrow, x0, nx);
+    int f = z ? x0 + __ffs(z) - 1 : kBig;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) f = min(f, __shfl_xor_sync(kFull, f, o));
+    if (lane == s) segfirst = f;
+  }
+  // Inclusive suffix minimum over segments (lane i: min over segments >= i).
+  int suf = segfirst;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_down_sync(kFull, suf, o);
+    if (lane + o < 32) suf = min(suf, t);
+  }
+
+  int carry_left = -1;  // last background before the segment (virtual at -1)
+  for (int s = 0; s < nseg; ++s) {
+    const int x0 = s * kSeg + lane * 16;
+    int after = __shfl_sync(kFull, suf, (s + 1) & 31);
+    if (s + 1 >= nseg) after = kBig;
+    after = min(after, nx);  // virtual background at nx
+    const uint32_t z = zero_bits<VEC>(mrow, x0, nx);
+    const int lastz = z ? x0 + 31 - __clz(z) : -1;
+    const int firstz = z ? x0 + __ffs(z) - 1 : kBig;
+    int incl = lastz;  // inclusive prefix max over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl = max(incl, t);
+    }
+    int left = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) left = -1;
+    left = max(left, carry_left);
+    int inclr = firstz;  // inclusive suffix min over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_down_sync(kFull, inclr, o);
+      if (lane + o < 32) inclr = min(inclr, t);
+    }
+    int right = __shfl_down_sync(kFull, inclr, 1);
+    if (lane == 31) right = kBig;
+    right = min(right, after);
+    carry_left = max(carry_left, __shfl_sync(kFull, incl, 31));
+
+    int lpos[16];
+    int L = left;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if ((z >> j) & 1u) L = x0 + j;
+      lpos[j] = L;
+    }
+    uint32_t g2[16];
+    int R = right;
+#pragma unroll
+    for (int j = 15; j >= 0; --j) {
+      if ((z >> j) & 1u) R = x0 + j;
+      const int x = x0 + j;
+      const int g = min(x - lpos[j], R - x);
+      g2[j] = (uint32_t)(g * g);
+    }
+    if (VEC && x0 + 16 <= nx) {
+      uint4* o4 = reinterpret_cast<uint4*>(orow + x0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o4[k] = make_uint4(g2[4 * k], g2[4 * k + 1], g2[4 * k + 2], g2[4 * k + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (x0 + j < nx) orow[x0 + j] = g2[j];
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t envelope_at(const uint32_t* __restrict__ col, int stride, int p,
+                                                int L) {
+  uint32_t best = col[p * stride];
+  if (best == 0) return 0;
+  const uint32_t b1 = (uint32_t)(p + 1) * (uint32_t)(p + 1);
+  const uint32_t b2 = (uint32_t)(L - p) * (uint32_t)(L - p);
+  best = min(best, min(b1, b2));
+  for (uint32_t k = 1; k * k < best; ++k) {
+    if ((uint32_t)p >= k) best = min(best, col[(p - (int)k) * stride] + k * k);
+    if (p + (int)k < L) best = min(best, col[(p + (int)k) * stride] + k * k);
+  }
+  return best;
+}
+
+// Column pass in shared memory. Tile: TX adjacent columns x the whole axis
+// (length L, stride sp between elements); blockIdx.y picks the other
+// coordinate (stride so). In place.
+template <int TX>
+__global__ void __launch_bounds__(256) edt_cols_kernel(uint32_t* __restrict__ data, int L, size_t sp,
+                                                       int nx, size_t so, int vec) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t* tile = reinterpret_cast<uint32_t*>(smem_raw);
+  const int x0 = blockIdx.x * TX;
+  uint32_t* base = data + (size_t)blockIdx.y * so + x0;
+  const int ncol = min(TX, nx - x0);
+  constexpr int Q = TX / 4;
+  for (int i = threadIdx.x; i < L * Q; i += blockDim.x) {
+    const int p = i / Q, qd = i % Q;
+    const uint32_t* src = base + (size_t)p * sp + qd * 4;
+    uint4 v;
+    if (vec && qd * 4 + 4 <= ncol) {
+      v = *reinterpret_cast<const uint4*>(src);
+    } else {
+      v.x = qd * 4 + 0 < ncol ? src[0] : 0u;
+      v.y = qd * 4 + 1 < ncol ? src[1] : 0u;
+      v.z = qd * 4 + 2 < ncol ? src[2] : 0u;
+      v.w = qd * 4 + 3 < ncol ? src[3] : 0u;
+    }
+    *reinterpret_cast<uint4*>(tile + p * TX + qd * 4) = v;
+  }
+  __syncthreads();
+  const int c = threadIdx.x % TX;
+  const int nrg = blockDim.x / TX;
+  if (c < ncol) {
+    for (int p = threadIdx.x / TX; p < L; p += nrg) base[(size_t)p * sp + c] = envelope_at(tile + c, TX, p, L);
+  }
+}
+
+// Column pass reading `in` and writing `out` directly (axes longer than the
+// shared-memory tile allows).
+__global__ void __launch_bounds__(256) edt_cols_global_kernel(const uint32_t* __restrict__ in,
+                                                              uint32_t* __restrict__ out, int L,
+                                                              size_t sp, int nx, size_t so,
+                                                              int rows_per_block) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (c >= nx) return;
+  const size_t off = (size_t)blockIdx.y * so + c;
+  const uint32_t* col = in + off;
+  const int p0 = blockIdx.z * rows_per_block;
+  const int p1 = min(L, p0 + rows_per_block);
+  for (int p = p0 + (threadIdx.x >> 5); p < p1; p += blockDim.x >> 5) {
+    uint32_t best = col[(size_t)p * sp];
+    if (best) {
+      const uint32_t b1 = (uint32_t)(p + 1) * (uint32_t)(p + 1);
+      const uint32_t b2 = (uint32_t)(L - p) * (uint32_t)(L - p);
+      best = min(best, min(b1, b2));
+      for (uint32_t k = 1; k * k < best; ++k) {
+        if ((uint32_t)p >= k) best = min(best, col[(size_t)(p - (int)k) * sp] + k * k);
+        if (p + (int)k < L) best = min(best, col[(size_t)(p + (int)k) * sp] + k * k);
+      }
+    }
+    out[off + (size_t)p * sp] = best;
+  }
+}
+
+template <int TX>
+cudaError_t launch_cols(const char* name, uint32_t* data, int L, size_t sp, int nx, size_t so,
+                        int nother, bool vec, cudaStream_t s) {
+  const int smem = L * TX * 4;
+  cudaError_t e = allow_smem((const void*)edt_cols_kernel<TX>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nx + TX - 1) / TX, nother);
+  {
+    TraceScope t(name, s);
+    edt_cols_kernel<TX><<<grid, 256, smem, s>>>(data, L, sp, nx, so, vec ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t col_pass(const char* name, uint32_t* data, int L, size_t sp, int nx, size_t so, int nother,
+                     uint32_t* tmp, size_t n, cudaStream_t s) {
+  const bool vec = (nx % 4) == 0;
+  if (L <= 512) return launch_cols<32>(name, data, L, sp, nx, so, nother, vec, s);
+  if (L <= 1024) return launch_cols<16>(name, data, L, sp, nx, so, nother, vec, s);
+  if (L <= 2048) return launch_cols<8>(name, data, L, sp, nx, so, nother, vec, s);
+  const int rpb = 64;
+  dim3 grid((nx + 31) / 32, nother, (L + rpb - 1) / rpb);
+  {
+    TraceScope t(name, s);
+    edt_cols_global_kernel<<<grid, 256, 0, s>>>(data, tmp, L, sp, nx, so, rpb);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(data, tmp, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace
+
+size_t edt_workspace_bytes(const Dims& d) {
+  const int longest = d.ndim == 3 ? (d.ny > d.nz ? d.ny : d.nz) : d.ny;
+  return longest > 2048 ? (size_t)d.n * sizeof(uint32_t) : 0;
+}
+
+cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
+                       cudaStream_t s) {
+  const uint32_t nrows = (uint32_t)d.ny * (uint32_t)d.nz;
+  const unsigned blocks = (nrows + 7) / 8;
+  {
+    TraceScope t("edt_rows_x", s);
+    if (d.nx % 16 == 0)
+      edt_rows_kernel<true><<<blocks, 256, 0, s>>>(mask, dt2, d.nx, nrows);
+    else
+      edt_rows_kernel<false><<<blocks, 256, 0, s>>>(mask, dt2, d.nx, nrows);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t plane = (size_t)d.nx * d.ny;
+  // y: columns of length ny, stride nx; one tile row per z.
+  e = col_pass("edt_cols_y", dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s);
+  if (e != cudaSuccess || d.ndim == 2) return e;
+  // z: columns of length nz, stride nx*ny; one tile row per y.
+  return col_pass("edt_cols_z", dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s);
+}
+
+}  // namespace ltk

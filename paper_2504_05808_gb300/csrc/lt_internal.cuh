@@ -1,0 +1,86 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lt.h"
+
+namespace ltk {
+
+// Array shape. nx, ny, nz <= 8192 and n = nx * ny * nz < 2^32.
+struct Dims {
+  int ndim;
+  int nx, ny, nz;
+  uint32_t n;
+};
+
+// First 256 bytes of every workspace.
+struct WsHeader {
+  uint32_t error;   // bit set of ERR_* found on the device
+  uint32_t touch;   // nonzero: two face-adjacent foreground voxels differ in label
+  uint32_t n_surv;  // number of centres kept by the ridge kernel
+  uint32_t reserved[61];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+enum : uint32_t { ERR_LABEL_RANGE = 1u, ERR_LABEL_OUTSIDE_MASK = 2u };
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Floor square root of v < 2^24: IEEE-rounded single-precision square root
+// of an exactly representable integer is within one of the floor; fix it.
+__device__ __forceinline__ uint32_t isqrt24(uint32_t v) {
+  uint32_t r = (uint32_t)sqrtf((float)v);
+  if (r * r > v) --r;
+  else if ((r + 1) * (r + 1) <= v) ++r;
+  return r;
+}
+
+// Per-object accumulators (structure of arrays in the workspace).
+struct ShapeAcc {
+  uint32_t* volume;
+  uint32_t* n_shell;
+  uint32_t* max_lt2;
+  unsigned long long* sum_lt;
+  unsigned long long* sum_shell_lt;
+};
+
+// ---- host launchers (each returns cudaSuccess or the launch error) ----
+// edt.cu
+size_t edt_workspace_bytes(const Dims& d);
+cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
+                       cudaStream_t s);
+// lt.cu
+uint32_t lt_table_r2cap(const Dims& d);
+size_t lt_workspace_bytes(const Dims& d);
+cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                      WsHeader* hdr, void* body, cudaStream_t s);
+// shape.cu
+size_t shape_workspace_bytes(uint32_t n_labels);
+cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                         const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
+                         const lt_object_stats* stats, cudaStream_t s);
+
+// Brackets one kernel launch with trace events when tracing is enabled
+// (see lt_trace_enable). Construct right before the launch; the destructor
+// records the end event after it.
+class TraceScope {
+ public:
+  TraceScope(const char* name, cudaStream_t s);
+  ~TraceScope();
+
+ private:
+  int slot_;
+  cudaStream_t s_;
+};
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+// Raise the dynamic shared-memory limit of a kernel once per device.
+cudaError_t allow_smem(const void* func, int bytes);
+
+}  // namespace ltk

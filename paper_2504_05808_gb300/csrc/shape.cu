@@ -1,0 +1,185 @@
+// Per-object sphericity and roundness on sm_103a (Sec. 4.1 and 4.2 of the
+// paper).
+//
+// shape_reduce: one thread per voxel. An object voxel contributes 1 to its
+// volume, round(sqrt(LT2) * 2^20) to the fixed-point LT sum, LT2 to the
+// maximum, and, when one of its face neighbours (4 in 2D, 6 in 3D) is outside
+// its object (other label, background or outside the array), the same to the
+// shell count and shell sum. Lanes of a warp cover 32 consecutive voxels of a
+// row; equal labels form runs, which are combined by a segmented warp scan so
+// that one lane per run issues the atomics. Integer sums make the result
+// independent of the order of the atomics.
+//
+// shape_finalize: one thread per label, FP64:
+//   3D  a = mean LT, c = 3V / (4 pi a^2)                          (Eq. 8)
+//       area = 2 pi a^2 (1 + (1 - e^2)/e artanh e), e = sqrt(1 - c^2/a^2)  c < a
+//       area = 2 pi a^2 (1 + c/(a e) arcsin e),     e = sqrt(1 - a^2/c^2)  c > a
+//       area = 4 pi a^2                                            c = a
+//       (Eqs. 6-7; the printed eccentricity lacks its square root)
+//       S = pi^(1/3) (6V)^(2/3) / area                             (Eq. 1)
+//   2D  b = A / (pi a); P_o = pi (3(a+b) - sqrt((3a+b)(a+3b)));  (Eqs. 9-10)
+//       P_c = 2 sqrt(pi A); S = P_c / P_o                          (Eqs. 2, 11)
+//   R = (shell LT sum / shell count) / sqrt(max LT2)               (Sec. 4.2)
+#include "lt_internal.cuh"
+
+namespace ltk {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kFixScale = 1048576.0f;  // 2^LT_FIXED_POINT_SHIFT
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __restrict__ labels,
+                                                           const uint32_t* __restrict__ lt2, Dims d,
+                                                           uint32_t n_labels, ShapeAcc acc,
+                                                           WsHeader* __restrict__ hdr) {
+  const int lane = threadIdx.x & 31;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool in = x < d.nx;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x : 0;
+  uint32_t l = in ? labels[v] : 0u;
+  if (__ballot_sync(kFull, l != 0) == 0) return;  // uniform per warp
+  const bool bad = l >= n_labels;
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(&hdr->error, ERR_LABEL_RANGE);
+  if (bad) l = 0;
+
+  uint32_t pk = 0, mx = 0;  // pk = count | shell count << 16
+  unsigned long long q = 0, qs = 0;
+  if (l) {
+    const uint32_t t = lt2[v];
+    const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
+    bool s = x == 0 || labels[v - 1] != l || x == d.nx - 1 || labels[v + 1] != l || y == 0 ||
+             labels[v - sy] != l || y == d.ny - 1 || labels[v + sy] != l;
+    if (NDIM == 3) s = s || z == 0 || labels[v - sz] != l || z == d.nz - 1 || labels[v + sz] != l;
+    pk = 1u | (s ? 1u << 16 : 0u);
+    mx = t;
+    q = qq;
+    qs = s ? qq : 0ull;
+  }
+  // segmented inclusive scan over runs of equal labels
+  const uint32_t lprev = __shfl_up_sync(kFull, l, 1);
+  int seg = (lane == 0 || lprev != l) ? lane : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, seg, o);
+    if (lane >= o) seg = max(seg, t);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(kFull, pk, o);
+    const unsigned long long b = __shfl_up_sync(kFull, q, o);
+    const unsigned long long c = __shfl_up_sync(kFull, qs, o);
+    const uint32_t m = __shfl_up_sync(kFull, mx, o);
+    if (lane - o >= seg) {
+      pk += a;
+      q += b;
+      qs += c;
+      mx = max(mx, m);
+    }
+  }
+  const uint32_t lnext = __shfl_down_sync(kFull, l, 1);
+  if (l && (lane == 31 || lnext != l)) {
+    atomicAdd(acc.volume + l, pk & 0xFFFFu);
+    atomicAdd(acc.n_shell + l, pk >> 16);
+    atomicAdd(acc.sum_lt + l, q);
+    atomicAdd(acc.sum_shell_lt + l, qs);
+    atomicMax(acc.max_lt2 + l, mx);
+  }
+}
+
+__device__ double spheroid_area(double a, double c) {
+  const double pi = 3.141592653589793;
+  if (c == a) return 4.0 * pi * a * a;
+  if (c < a) {
+    const double e = sqrt(1.0 - (c * c) / (a * a));
+    return 2.0 * pi * a * a * (1.0 + (1.0 - e * e) / e * atanh(e));
+  }
+  const double e = sqrt(1.0 - (a * a) / (c * c));
+  return 2.0 * pi * a * a * (1.0 + c / (a * e) * asin(e));
+}
+
+template <int NDIM>
+__global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __restrict__ S,
+                                      float* __restrict__ R, lt_object_stats st) {
+  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_labels) return;
+  const uint32_t V = l ? acc.volume[l] : 0u;
+  const uint32_t ns = l ? acc.n_shell[l] : 0u;
+  const uint32_t mx = l ? acc.max_lt2[l] : 0u;
+  const unsigned long long sl = l ? acc.sum_lt[l] : 0ull, ss = l ? acc.sum_shell_lt[l] : 0ull;
+  if (st.volume) st.volume[l] = V;
+  if (st.n_shell) st.n_shell[l] = ns;
+  if (st.max_lt2) st.max_lt2[l] = mx;
+  if (st.sum_lt) st.sum_lt[l] = sl;
+  if (st.sum_shell_lt) st.sum_shell_lt[l] = ss;
+  double sph = nan(""), rnd = nan("");
+  if (V > 0) {
+    const double pi = 3.141592653589793;
+    const double inv = 1.0 / 1048576.0;
+    const double Vd = (double)V;
+    const double a = (double)sl * inv / Vd;
+    if (NDIM == 3) {
+      const double c = 3.0 * Vd / (4.0 * pi * a * a);
+      const double k = cbrt(6.0 * Vd);
+      sph = cbrt(pi) * k * k / spheroid_area(a, c);
+    } else {
+      const double b = Vd / (pi * a);
+      const double po = pi * (3.0 * (a + b) - sqrt((3.0 * a + b) * (a + 3.0 * b)));
+      sph = 2.0 * sqrt(pi * Vd) / po;
+    }
+    rnd = ((double)ss * inv / (double)ns) / sqrt((double)mx);
+  }
+  if (S) S[l] = (float)sph;
+  if (R) R[l] = (float)rnd;
+}
+
+}  // namespace
+
+static size_t acc_bytes(uint32_t n) {
+  return 3 * align_up((size_t)n * 4) + 2 * align_up((size_t)n * 8);
+}
+
+size_t shape_workspace_bytes(uint32_t n_labels) { return acc_bytes(n_labels); }
+
+cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                         const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
+                         const lt_object_stats* stats, cudaStream_t s) {
+  char* p = reinterpret_cast<char*>(body);
+  ShapeAcc acc;
+  acc.volume = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.n_shell = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.max_lt2 = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.sum_lt = reinterpret_cast<unsigned long long*>(p);
+  p += align_up((size_t)n_labels * 8);
+  acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
+  cudaError_t e = cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
+  if (e != cudaSuccess) return e;
+  dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
+  {
+    TraceScope t("shape_reduce", s);
+    if (d.ndim == 3)
+      shape_reduce_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+    else
+      shape_reduce_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  lt_object_stats st = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (stats) st = *stats;
+  const unsigned blocks = (n_labels + 255) / 256;
+  {
+    TraceScope t("shape_finalize", s);
+    if (d.ndim == 3)
+      shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
+    else
+      shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ltk

@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/lt.h declares, and rejects bad arguments before any
+CUDA call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lt.h")
+
+
+@pytest.fixture(scope="module")
+def lt():
+    import __graft_entry__
+    __graft_entry__._cuda_builder().build()
+    import paper_2504_05808_gb300 as mod
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(lt_[a-z0-9_]+)\s*\(", text,
+                       flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lt):
+    names = declared_functions()
+    assert len(names) >= 13
+    lib = ctypes.CDLL(lt.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lt.SIGNATURES)
+
+
+def test_status_strings_and_version(lt):
+    for code in range(8):
+        s = lt.lib.lt_status_string(code)
+        assert s and s != b"unknown status"
+    assert lt.lib.lt_status_string(99) == b"unknown status"
+    assert lt.lib.lt_version() == 0x000100
+
+
+def test_workspace_sizes(lt):
+    L = lt.lib
+    n = 512 ** 3
+    # local thickness: header + lookup table + 8 bytes per voxel
+    ws = L.lt_local_thickness_workspace_size(3, 512, 512, 512)
+    assert 8 * n < ws < 8 * n + (4 << 20)
+    assert L.lt_edt_workspace_size(3, 512, 512, 512) == 0
+    assert L.lt_edt_workspace_size(2, 100, 3000, 1) == 4 * 300000
+    assert L.lt_shape_workspace_size(1000) >= 28 * 1000
+    assert L.lt_measure_workspace_size(100, 3, 512, 512, 512) >= ws
+    host = L.lt_measure_host_workspace_size(100, 3, 64, 64, 64)
+    assert host >= L.lt_measure_workspace_size(100, 3, 64, 64, 64) + 13 * 64 ** 3
+    # invalid dimensions give 0
+    assert L.lt_local_thickness_workspace_size(2, 10, 10, 2) == 0
+    assert L.lt_local_thickness_workspace_size(3, 8193, 1, 1) == 0
+    assert L.lt_local_thickness_workspace_size(4, 1, 1, 1) == 0
+
+
+def test_argument_errors_need_no_gpu(lt):
+    L = lt.lib
+    E = {v: k for k, v in lt.STATUS_NAMES.items()}
+    assert L.lt_edt(None, None, 3, 0, 4, 4, None, 0, None) == E["LT_ERR_DIMS"]
+    assert L.lt_edt(None, None, 2, 4, 4, 3, None, 0, None) == E["LT_ERR_DIMS"]
+    assert L.lt_edt(None, None, 5, 4, 4, 4, None, 0, None) == E["LT_ERR_INVALID_ARG"]
+    assert L.lt_edt(None, None, 3, 4096, 4096, 4096, None, 0, None) == E["LT_ERR_DIMS"]
+    assert L.lt_edt(None, None, 3, 4, 4, 4, None, 0, None) == E["LT_ERR_INVALID_ARG"]
+    assert L.lt_local_thickness(None, None, None, 3, 4, 4, 4, None, 0, None) == E["LT_ERR_INVALID_ARG"]
+    assert L.lt_shape_measures(None, None, 0, 3, 4, 4, 4, None, 0, None, None, None, None) == \
+        E["LT_ERR_INVALID_ARG"]
+    # misaligned pointers are rejected before use
+    assert L.lt_edt(ctypes.c_void_p(17), ctypes.c_void_p(32), 3, 4, 4, 4, None, 0, None) == \
+        E["LT_ERR_INVALID_ARG"]
+    assert L.lt_measure_host(None, None, 3, 3, 4, 4, 4, None, 0, None, None, None) == \
+        E["LT_ERR_INVALID_ARG"]
+    assert L.lt_workspace_status(None, 0, None) == E["LT_ERR_WORKSPACE"]
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """The library package neither imports nor links the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_2504_05808_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "lt_oracle" not in text, f

@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: DT2 and LT2 bit-exact; sphericity and roundness within 1e-5 relative
+(float32 outputs of FP64 formulas on fixed-point sums; each LT value enters
+the sums as round(sqrtf(LT2) * 2^20), off by at most 2^-24 relative plus
+2^-21 absolute); integer per-object counts exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("built_cpu_parts")]
+
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_05808_gb300 as mod
+    return mod
+
+
+def dev_u32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def host_u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def gpu_pipeline(lt, mask, labels, n_labels, separate=False):
+    import torch
+    m = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
+    l = dev_u32(labels)
+    dt2 = torch.empty(mask.shape, dtype=torch.int32, device="cuda")
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n_labels, dtype=torch.float32, device="cuda")
+    R = torch.empty_like(S)
+    stats = {k: torch.empty(n_labels, dtype=torch.int32, device="cuda")
+             for k in ("volume", "n_shell", "max_lt2")}
+    stats.update({k: torch.empty(n_labels, dtype=torch.int64, device="cuda")
+                  for k in ("sum_lt", "sum_shell_lt")})
+    if separate:
+        lt.lt_edt(m, dt2)
+        ws = lt.lt_local_thickness(dt2, l, lt2)
+        lt.lt_workspace_status(ws)
+        ws = lt.lt_shape_measures(l, lt2, n_labels, S, R, stats)
+    else:
+        ws = lt.lt_measure(m, l, n_labels, dt2, lt2, S, R)
+    lt.lt_workspace_status(ws)
+    torch.cuda.synchronize()
+    st = {k: v.cpu().numpy() for k, v in stats.items()}
+    return host_u32(dt2), host_u32(lt2), S.cpu().numpy(), R.cpu().numpy(), st
+
+
+def assert_close(got, ref, what):
+    ref = np.asarray(ref, dtype=np.float64)
+    got = np.asarray(got, dtype=np.float64)
+    assert np.array_equal(np.isnan(got), np.isnan(ref)), what + ": NaN pattern"
+    f = ~np.isnan(ref)
+    err = np.abs(got[f] - ref[f]) / np.maximum(np.abs(ref[f]), 1e-30)
+    assert err.size == 0 or err.max() <= REL_TOL, f"{what}: max rel err {err.max():.3g}"
+
+
+def check_full(lt, mask, labels, n_labels, separate=False):
+    d, l2, S, R, st = gpu_pipeline(lt, mask, labels, n_labels, separate)
+    d_ref, l_ref, S_ref, R_ref = oracle.pipeline(mask, labels, n_labels)
+    assert np.array_equal(d, d_ref), "DT2"
+    assert np.array_equal(l2, l_ref), "LT2"
+    assert_close(S, S_ref, "sphericity")
+    assert_close(R, R_ref, "roundness")
+    if separate:
+        ost = oracle.object_stats(labels, l_ref, n_labels)
+        for k in ("volume", "n_shell", "max_lt2"):
+            assert np.array_equal(st[k].astype(np.int64) & 0xFFFFFFFF, ost[k]), k
+        for k in ("sum_lt", "sum_shell_lt"):
+            got = st[k].astype(np.float64) / 2.0 ** 20
+            n = ost["volume"] if k == "sum_lt" else ost["n_shell"]
+            # per voxel: single-precision sqrt (<= 2^-24 relative) then rounding
+            # to 2^-20 (<= 2^-21 absolute)
+            assert np.all(np.abs(got - ost[k]) <= n * 2.0 ** -21 + ost[k] * 2.0 ** -23), k
+    return d, l2
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_random_small_masks(lt, ndim):
+    """Ragged sizes (not multiples of any tile), random density, labelled by
+    connected component; every third case splits components so that
+    different labels touch."""
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(40 + ndim)
+    for t in range(25):
+        if ndim == 2:
+            shape = (int(rng.integers(1, 90)), int(rng.integers(1, 90)))
+        else:
+            shape = tuple(int(v) for v in rng.integers(1, 30, size=3))
+        f = ndi.gaussian_filter(rng.random(shape), rng.uniform(0.5, 2.5))
+        mask = (f > np.quantile(f, rng.uniform(0.2, 0.8))).astype(np.uint8)
+        labels = ndi.label(mask)[0].astype(np.uint32)
+        if t % 3 == 0 and labels.max() > 0:
+            labels[(labels > 0) & (rng.random(shape) < 0.2)] = labels.max() + 1
+        if t % 4 == 1:  # unlabelled foreground
+            labels[(labels > 0) & (rng.random(shape) < 0.1)] = 0
+        check_full(lt, mask, labels, int(labels.max()) + 2, separate=(t % 2 == 0))
+
+
+def test_ellipses_2d_256(lt):
+    m, l, n = synth.workload("ellipses_2d_256", 0)
+    check_full(lt, m, l, n, separate=True)
+
+
+def test_ellipsoids_3d_128(lt):
+    m, l, n = synth.workload("ellipsoids_3d_128", 0)
+    check_full(lt, m, l, n, separate=True)
+    check_full(lt, m, l, n)
+
+
+def test_long_axes_use_every_column_path(lt):
+    """Axis lengths that select the 32-, 16- and 8-column shared-memory tiles
+    and the global-memory column pass."""
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(3)
+    for shape in [(700, 37), (1500, 21), (2500, 9), (600, 20, 24), (1100, 9, 17)]:
+        f = ndi.gaussian_filter(rng.random(shape), 4.0)
+        mask = (f > np.quantile(f, 0.3)).astype(np.uint8)
+        labels = ndi.label(mask)[0].astype(np.uint32)
+        check_full(lt, mask, labels, int(labels.max()) + 1)
+
+
+def test_degenerate_inputs(lt):
+    cases = []
+    cases.append((np.zeros((17, 33), np.uint8), None))
+    cases.append((np.ones((9, 10, 11), np.uint8), None))
+    one = np.zeros((5, 6, 7), np.uint8)
+    one[2, 3, 4] = 1
+    cases.append((one, None))
+    cases.append((np.ones((1, 1), np.uint8), None))
+    cases.append((np.ones((1, 64), np.uint8), None))
+    cases.append((np.ones((64, 1), np.uint8), None))
+    cases.append((np.ones((40, 1, 1), np.uint8), None))
+    line = np.zeros((8, 8, 8), np.uint8)
+    line[4, 4, :] = 1
+    cases.append((line, None))
+    for mask, labels in cases:
+        labels = mask.astype(np.uint32) if labels is None else labels
+        check_full(lt, mask, labels, 3)
+
+
+def test_digital_balls(lt):
+    for r in (5, 10, 20):
+        n = 2 * r + 5
+        g = np.indices((n, n, n)) - n // 2
+        ball = ((g ** 2).sum(0) <= r * r).astype(np.uint8)
+        _, l2, S, R, _ = gpu_pipeline(lt, ball, ball.astype(np.uint32), 2)
+        assert np.all(l2[ball > 0] == l2.max())
+        assert abs(R[1] - 1.0) <= 1e-6 and S[1] < 1.0
+
+
+def test_full_size_particles_512_sampled(lt):
+    """The 512^3 particle volume in the benchmark's launch configuration
+    (lt_measure on the whole volume). The oracle checks sampled objects one
+    by one (DT2 and LT2 of every voxel of each sampled object, and its S and
+    R); properties that hold at any size are checked on the whole volume."""
+    mask, labels, n = synth.workload("particles_3d_512", 0)
+    d, l2, S, R, _ = gpu_pipeline(lt, mask, labels, n)
+    rng = np.random.default_rng(0)
+    vols = np.bincount(labels.reshape(-1), minlength=n)
+    present = np.flatnonzero(vols[1:]) + 1
+    pick = list(rng.choice(present, 60, replace=False)) + list(present[np.argsort(vols[present])[-8:]])
+    ref = oracle.objects_dt2_lt2(mask, labels, pick)
+    for lab, (idx, dd, ll) in ref.items():
+        assert np.array_equal(d.reshape(-1)[idx], dd), f"DT2 of object {lab}"
+        assert np.array_equal(l2.reshape(-1)[idx], ll), f"LT2 of object {lab}"
+        s_ref, r_ref = oracle.object_measures_from_voxels(labels, idx, ll)
+        assert_close(S[lab], s_ref, f"S of object {lab}")
+        assert_close(R[lab], r_ref, f"R of object {lab}")
+    on = labels != 0
+    assert np.array_equal(d == 0, mask == 0)
+    assert np.all(l2[on] >= d[on]) and np.all(l2[~on] == 0)
+    f = ~np.isnan(S)
+    assert np.all(S[f] <= 1 + 1e-6) and np.all(R[f] <= 1 + 1e-6) and np.all(R[f] > 0)
+    assert np.isnan(S[0]) and np.array_equal(np.isnan(S[1:]), vols[1:] == 0)
+
+
+def test_device_detected_errors(lt):
+    import torch
+    m, l, n = synth.workload("ellipses_2d_256", 2)
+    bad = l.copy()
+    bad[0, 0] = 1  # a labelled voxel outside the mask
+    mt = torch.from_numpy(m).cuda()
+    dt2 = torch.empty(m.shape, dtype=torch.int32, device="cuda")
+    lt2 = torch.empty_like(dt2)
+    lt.lt_edt(mt, dt2)
+    ws = lt.lt_local_thickness(dt2, dev_u32(bad), lt2)
+    with pytest.raises(lt.LTError) as e:
+        lt.lt_workspace_status(ws)
+    assert e.value.status == 5
+    # labels beyond n_labels are reported and skipped
+    ws = lt.lt_local_thickness(dt2, dev_u32(l), lt2)
+    lt.lt_workspace_status(ws)
+    S = torch.empty(5, dtype=torch.float32, device="cuda")
+    ws = lt.lt_shape_measures(dev_u32(l), lt2, 5, S, None)
+    with pytest.raises(lt.LTError) as e:
+        lt.lt_workspace_status(ws)
+    assert e.value.status == 4
+    _, l_ref, S_ref, _ = oracle.pipeline(m, np.where(l < 5, l, 0).astype(np.uint32), 5)
+    assert_close(S.cpu().numpy(), S_ref, "S with out-of-range labels skipped")
+
+
+def test_host_buffer_entry_matches_device_path(lt):
+    import torch
+    m, l, n = synth.workload("ellipsoids_3d_128", 1)
+    _, _, S_dev, R_dev, _ = gpu_pipeline(lt, m, l, n)
+    mh = torch.from_numpy(m).pin_memory()
+    lh = torch.from_numpy(l.view(np.int32)).pin_memory()
+    Sh = torch.empty(n, dtype=torch.float32).pin_memory()
+    Rh = torch.empty(n, dtype=torch.float32).pin_memory()
+    ws = lt.workspace(lt.lt_measure_host_workspace_size(n, m.shape), "cuda")
+    lt.lt_measure_host(mh, lh, n, Sh, Rh, ws)
+    assert np.array_equal(Sh.numpy(), S_dev, equal_nan=True)
+    assert np.array_equal(Rh.numpy(), R_dev, equal_nan=True)
+
+
+def test_repeated_calls_reuse_workspace(lt):
+    """Same workspace, different volumes: results do not leak across calls."""
+    import torch
+    ws = None
+    for seed in (3, 4, 3):
+        m, l, n = synth.workload("ellipses_2d_256", seed)
+        mt, lt_ = torch.from_numpy(m).cuda(), dev_u32(l)
+        dt2 = torch.empty(m.shape, dtype=torch.int32, device="cuda")
+        lt2 = torch.empty_like(dt2)
+        S = torch.empty(64, dtype=torch.float32, device="cuda")
+        R = torch.empty_like(S)
+        if ws is None:
+            ws = lt.workspace(lt.lib.lt_measure_workspace_size(64, 2, 256, 256, 1), "cuda")
+        lt.lt_measure(mt, lt_, 64, dt2, lt2, S, R, ws=ws)
+        lt.lt_workspace_status(ws)
+        _, _, S_ref, R_ref = oracle.pipeline(m, l, 64)
+        assert_close(S.cpu().numpy(), S_ref, "S")
+        assert_close(R.cpu().numpy(), R_ref, "R")
