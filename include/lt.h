@@ -143,6 +143,27 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
                             float* sphericity, float* roundness, const lt_object_stats* stats,
                             void* stream);
 
+/* ------------------------------------------- shape measures, no allocation --
+ * Same computation and outputs as lt_shape_measures, for callers that cannot
+ * allocate device memory: code that receives device buffers from another
+ * framework but has no allocator of its own (plugins, callbacks inside
+ * someone else's pipeline), and latency-critical loops that must not call
+ * cudaMalloc after start-up because it can synchronise the whole device.
+ * The paper has no counterpart; this is a deployment convenience.
+ * Scratch: a fixed array in device memory that belongs to the library (every
+ * GPU that loads the library holds it until the process exits), large enough
+ * for LT_STATIC_MAX_LABELS labels. n_labels above that returns
+ * LT_ERR_WORKSPACE without enqueuing anything.
+ * The first call on each device looks up the array's device address (a
+ * one-time set-up); make that first call before any stream capture.
+ * All calls share the one array: calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Labels >= n_labels are skipped but, unlike lt_shape_measures, not reported. */
+#define LT_STATIC_MAX_LABELS 131072u
+lt_status lt_shape_measures_static(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                                   int ndim, int64_t nx, int64_t ny, int64_t nz, float* sphericity,
+                                   float* roundness, const lt_object_stats* stats, void* stream);
+
 /* ------------------------------------------------------------- pipeline --
  * lt_edt, lt_local_thickness and lt_shape_measures in sequence on one
  * workspace. dt2 and lt2 are outputs (device, one uint32 per voxel each). */

@@ -42,6 +42,7 @@ SIGNATURES = {
     "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
     "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
+    "lt_shape_measures_static": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp]),
     "lt_trace_enable": (_i32, [_i32]),
     "lt_trace_summary": (_i32, [_vp, _i32]),
 }

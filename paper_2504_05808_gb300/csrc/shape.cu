@@ -183,3 +183,92 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
 }
 
 }  // namespace ltk
+
+// ------------------------------------------------------------------------
+// lt_shape_measures_static: the shape measures with library-owned scratch,
+// for callers that cannot allocate device memory. The scratch (workspace
+// header + per-label accumulators for LT_STATIC_MAX_LABELS labels) is one
+// file-scope device array; host code never dereferences its name, it asks the
+// runtime for the array's device address once per device and passes that
+// address to the same launch sequence as lt_shape_measures.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes =
+    sizeof(ltk::WsHeader) + 3 * ((LT_STATIC_MAX_LABELS * 4 + 255) / 256 * 256) +
+    2 * ((LT_STATIC_MAX_LABELS * 8 + 255) / 256 * 256);
+
+static __device__ __align__(256) unsigned char g_shape_scratch[kStaticScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};
+
+// Device address of g_shape_scratch on the current device (looked up on the
+// first call per device), or nullptr on failure.
+void* static_scratch() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_shape_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  return g_scratch_addr[dev];
+}
+
+bool static_ptr_ok(const void* p) {
+  if (!p || (reinterpret_cast<uintptr_t>(p) % 16) != 0) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return false;
+  return cur == a.device || cudaSetDevice(a.device) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lt_status lt_shape_measures_static(const uint32_t* labels, const uint32_t* lt2,
+                                              uint32_t n_labels, int ndim, int64_t nx, int64_t ny,
+                                              int64_t nz, float* sphericity, float* roundness,
+                                              const lt_object_stats* stats, void* stream) {
+  if (ndim != 2 && ndim != 3) return LT_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 8192 || ny > 8192 || nz > 8192) return LT_ERR_DIMS;
+  if (ndim == 2 && nz != 1) return LT_ERR_DIMS;
+  const uint64_t n = (uint64_t)nx * (uint64_t)ny * (uint64_t)nz;
+  if (n >= (1ull << 32)) return LT_ERR_DIMS;
+  if (n_labels == 0) return LT_ERR_INVALID_ARG;
+  if (n_labels > LT_STATIC_MAX_LABELS) return LT_ERR_WORKSPACE;
+  if (!static_ptr_ok(labels) || !static_ptr_ok(lt2)) return LT_ERR_INVALID_ARG;
+  if (sphericity && !static_ptr_ok(sphericity)) return LT_ERR_INVALID_ARG;
+  if (roundness && !static_ptr_ok(roundness)) return LT_ERR_INVALID_ARG;
+  if (stats) {
+    const void* arr[5] = {stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt, stats->sum_shell_lt};
+    for (const void* p : arr)
+      if (p && !static_ptr_ok(p)) return LT_ERR_INVALID_ARG;
+  }
+  void* scratch = static_scratch();
+  if (!scratch) return LT_ERR_CUDA;
+  ltk::Dims d;
+  d.ndim = ndim;
+  d.nx = (int)nx;
+  d.ny = (int)ny;
+  d.nz = (int)nz;
+  d.n = (uint32_t)n;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  ltk::WsHeader* hdr = reinterpret_cast<ltk::WsHeader*>(scratch);
+  // the array keeps the previous call's contents: clear the header here; the
+  // accumulators are cleared by shape_launch
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(ltk::WsHeader), s);
+  if (e == cudaSuccess)
+    e = ltk::shape_launch(labels, lt2, n_labels, d, hdr, hdr + 1, sphericity, roundness, stats, s);
+  return e == cudaSuccess ? LT_OK : LT_ERR_CUDA;
+}
