@@ -204,7 +204,8 @@ def main():
     for _ in range(max(3, args.warmup)):
         lt.lt_measure(m, l, n_labels, dt2, lt2, S, R, ws=ws)
     lt.lt_workspace_status(ws)
-    n_surv = int(ws[8:12].view(torch.int32).item())
+    hdr = ws[:16].view(torch.int32).cpu()
+    n_surv = int(hdr[2].item()) + int(hdr[3].item())
 
     clocks = ClockSampler(local)
     clocks.start()

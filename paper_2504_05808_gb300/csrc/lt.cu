@@ -14,16 +14,26 @@
 //    B(c) is a subset of B(c + d) exactly when r_{c+d}^2 >= M(d, r_c^2); such a
 //    c (same label as c + d) is dropped. M > r^2, so the container ranks
 //    higher. M depends only on the class of d (1, 2 or 3 nonzero
-//    coordinates) by the symmetry of the lattice ball, and is tabulated on
-//    the device for r^2 up to 2^18; larger centres are never dropped.
+//    coordinates) by the symmetry of the lattice ball. It is tabulated for
+//    r^2 <= 2^18; larger centres are never dropped.
 // 2. Crescent painting. A kept centre c picks one higher-ranked same-label
-//    neighbour D (the one whose ball reaches farthest past c's, if any) and
-//    raises LT2 only on voxels of B(c) outside B(D).
+//    neighbour D and raises LT2 only on voxels of B(c) outside B(D).
 // Exactness, by induction down the rank order: every object voxel x in any
 // B(c) ends with LT2(x) >= r_c^2. If c was dropped, x lies in a higher-ranked
 // ball of radius >= r_c. If c is kept, x is either painted by c or lies in
 // B(D) with r_D >= r_c. The highest-ranked centre paints its whole ball.
 // Since only true ball radii are painted, LT2 is exactly the maximum.
+//
+// Crescent tables. B(c) \ B(c + d) depends only on (r_c^2, d, r_D^2), and a
+// signed permutation of the axes maps it onto the crescent of the canonical
+// offset of d's class, (1,0,0), (1,1,0) or (1,1,1). A kept centre has
+// r_c^2 <= r_D^2 < M(d, r_c^2), about 2 |d| r_c values of r_D^2, so for
+// r_c^2 <= 144 every crescent fits a table of 1.4 M voxel offsets. Such a
+// centre paints its tabulated crescent voxel by voxel (lanes of a warp share
+// the voxels of 32 centres). The dominant neighbour D is the one whose
+// crescent is smallest (for larger radii: the one whose ball comes closest to
+// containing c's). Centres with r^2 > 144, without a higher-ranked neighbour,
+// or in 2D paint row by row instead.
 //
 // Voxels strictly inside B(c) are foreground (DT2(c) is the distance to the
 // nearest background), so only points with |y - c|^2 == r_c^2 may be
@@ -32,8 +42,13 @@
 // face-adjacent foreground voxels carry different labels (checked by the
 // ridge kernel, flag `touch`) every foreground ball voxel has c's label and
 // the label test is skipped.
+//
+// The tables are built once per process on the host and copied once per
+// device into the arrays below (about 13 MiB of device memory).
 #include <algorithm>
 #include <climits>
+#include <mutex>
+#include <vector>
 
 #include "lt_internal.cuh"
 
@@ -41,196 +56,496 @@ namespace ltk {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint32_t kTableCap = 1u << 18;
+constexpr uint32_t kMCap = 1u << 18;  // containment table covers r^2 <= 2^18
+constexpr int kCresT = 144;           // crescent tables cover r^2 <= 144
+constexpr int kCresMaxCombos = 12288;
+constexpr int kCresMaxVoxels = 1 << 21;
 constexpr uint32_t kNoDominant = 31u;
+constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 
-// raw[cls][n] = max over sorted lattice points (y1 >= y2 >= y3 >= 0) with
-// |y|^2 = n of |y|^2 + 2 (sum of the cls largest |y_i|) + cls: the largest
-// |y - d|^2 among the signed permutations of y for d of class cls.
-__global__ void mtable_points_kernel(uint32_t* __restrict__ raw, uint32_t cap, int R, int ndim) {
-  const size_t total = (size_t)(R + 1) * (R + 1);
-  const size_t stride = (size_t)(cap + 1);
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t y1 = (uint32_t)(t / (R + 1)), y2 = (uint32_t)(t % (R + 1));
-    if (y2 > y1) continue;
-    const uint32_t n12 = y1 * y1 + y2 * y2;
-    if (n12 > cap) continue;
-    if (ndim == 2) {
-      atomicMax(&raw[n12], n12 + 2 * y1 + 1);
-      atomicMax(&raw[stride + n12], n12 + 2 * (y1 + y2) + 2);
-    } else {
+__device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
+__device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
+__device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
+__device__ uint32_t g_cres_start[kCresMaxCombos + 1];
+// canonical crescent voxels: (x+128) | (y+128) << 8 | (z+128) << 16 |
+// (on the sphere |y|^2 == r^2) << 24
+__device__ uint32_t g_cres_vox[kCresMaxVoxels];
+
+// ------------------------------------------------------------ host tables
+struct HostTables {
+  std::vector<uint32_t> m3, m2, base, start, vox;
+  bool ok = false;
+};
+
+int isqrt_host(int64_t v) {
+  int64_t r = 0;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return (int)r;
+}
+
+HostTables* build_host_tables() {
+  HostTables* t = new HostTables();
+  const uint32_t cap = kMCap;
+  t->m3.assign(3 * (size_t)(cap + 1), 0u);
+  t->m2.assign(2 * (size_t)(cap + 1), 0u);
+  const int R = isqrt_host(cap);
+  // sorted lattice points y1 >= y2 (>= y3) >= 0: the largest |y - d|^2 over
+  // the signed permutations of y is |y|^2 + 2 (sum of the cls largest |y_i|) + cls
+  for (uint32_t y1 = 0; y1 <= (uint32_t)R; ++y1)
+    for (uint32_t y2 = 0; y2 <= y1; ++y2) {
+      const uint32_t n12 = y1 * y1 + y2 * y2;
+      if (n12 > cap) break;
+      t->m2[n12] = std::max(t->m2[n12], n12 + 2 * y1 + 1);
+      t->m2[(cap + 1) + n12] = std::max(t->m2[(cap + 1) + n12], n12 + 2 * (y1 + y2) + 2);
       for (uint32_t y3 = 0; y3 <= y2; ++y3) {
         const uint32_t n = n12 + y3 * y3;
         if (n > cap) break;
-        atomicMax(&raw[n], n + 2 * y1 + 1);
-        atomicMax(&raw[stride + n], n + 2 * (y1 + y2) + 2);
-        atomicMax(&raw[2 * stride + n], n + 2 * (y1 + y2 + y3) + 3);
+        t->m3[n] = std::max(t->m3[n], n + 2 * y1 + 1);
+        t->m3[(cap + 1) + n] = std::max(t->m3[(cap + 1) + n], n + 2 * (y1 + y2) + 2);
+        t->m3[2 * (size_t)(cap + 1) + n] = std::max(t->m3[2 * (size_t)(cap + 1) + n], n + 2 * (y1 + y2 + y3) + 3);
       }
     }
-  }
+  // prefix maximum over n: M(d, r^2) = max over |y|^2 <= r^2
+  for (int k = 0; k < 3; ++k)
+    for (uint32_t n = 1; n <= cap; ++n)
+      t->m3[k * (size_t)(cap + 1) + n] = std::max(t->m3[k * (size_t)(cap + 1) + n], t->m3[k * (size_t)(cap + 1) + n - 1]);
+  for (int k = 0; k < 2; ++k)
+    for (uint32_t n = 1; n <= cap; ++n)
+      t->m2[k * (size_t)(cap + 1) + n] = std::max(t->m2[k * (size_t)(cap + 1) + n], t->m2[k * (size_t)(cap + 1) + n - 1]);
+  // crescents B(0, r^2) \ B(d, rd^2) for the canonical offsets
+  const int dl[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 1, 1}};
+  t->base.assign(3 * (kCresT + 1), 0u);
+  for (int k = 0; k < 3; ++k)
+    for (int r2 = 0; r2 <= kCresT; ++r2) {
+      t->base[k * (kCresT + 1) + r2] = (uint32_t)t->start.size();
+      const int Rr = isqrt_host(r2);
+      const uint32_t mlim = t->m3[k * (size_t)(cap + 1) + r2];
+      for (uint32_t rd2 = (uint32_t)r2; rd2 < mlim; ++rd2) {
+        t->start.push_back((uint32_t)t->vox.size());
+        for (int z = -Rr; z <= Rr; ++z)
+          for (int y = -Rr; y <= Rr; ++y)
+            for (int x = -Rr; x <= Rr; ++x) {
+              const int n = x * x + y * y + z * z;
+              if (n > r2) continue;
+              const int e = (x - dl[k][0]) * (x - dl[k][0]) + (y - dl[k][1]) * (y - dl[k][1]) +
+                            (z - dl[k][2]) * (z - dl[k][2]);
+              if (e <= (int)rd2) continue;
+              t->vox.push_back((uint32_t)(x + 128) | ((uint32_t)(y + 128) << 8) |
+                               ((uint32_t)(z + 128) << 16) | ((n == r2 ? 1u : 0u) << 24));
+            }
+      }
+    }
+  t->start.push_back((uint32_t)t->vox.size());
+  t->ok = t->start.size() <= (size_t)kCresMaxCombos + 1 && t->vox.size() <= (size_t)kCresMaxVoxels;
+  return t;
 }
 
-// In-place prefix maximum over n of one table row (one 1024-thread block per
-// class): M(d, r^2) = max over n <= r^2 of raw[n].
-__global__ void __launch_bounds__(1024) mtable_prefix_kernel(uint32_t* __restrict__ tab, uint32_t cap) {
-  __shared__ uint32_t part[1024];
-  uint32_t* row = tab + (size_t)blockIdx.x * (cap + 1);
-  const uint32_t n = cap + 1;
-  const uint32_t chunk = (n + 1023) / 1024;
-  const uint32_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
-  uint32_t m = 0;
-  for (uint32_t i = lo; i < hi; ++i) m = max(m, row[i]);
-  part[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] = max(part[threadIdx.x], t);
-    __syncthreads();
-  }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (uint32_t i = lo; i < hi; ++i) {
-    run = max(run, row[i]);
-    row[i] = run;
-  }
+std::mutex g_tables_mu;
+HostTables* g_host_tables = nullptr;
+bool g_tables_on[64] = {false};
+
+// Copies the tables to the current device on its first use.
+cudaError_t ensure_tables() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(g_tables_mu);
+  if (g_tables_on[dev]) return cudaSuccess;
+  if (!g_host_tables) g_host_tables = build_host_tables();
+  const HostTables& h = *g_host_tables;
+  if (!h.ok) return cudaErrorInvalidValue;
+  e = cudaMemcpyToSymbol(g_m3, h.m3.data(), h.m3.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_m2, h.m2.data(), h.m2.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_base, h.base.data(), h.base.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_start, h.start.data(), h.start.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_vox, h.vox.data(), h.vox.size() * 4);
+  if (e == cudaSuccess) g_tables_on[dev] = true;
+  return e;
 }
 
-// One thread per voxel: clears LT2, validates labels against the mask, sets
-// the `touch` flag, applies the containment test and appends kept centres.
-// A CTA covers 256 x-positions of kRidgeRows rows; kept centres collect in
-// shared memory and leave with one global atomic per CTA.
+__device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd2) {
+  return g_cres_base[cls * (kCresT + 1) + r2] + (rd2 - r2);
+}
+
+// ---------------------------------------------------------- ridge kernel
+// Clears LT2, validates labels against the mask, sets the `touch` flag,
+// applies the containment test and appends kept centres.
+//
+// A CTA owns a 32 x 8 (x, y) column tile and marches along z through
+// kRidgeZ planes, keeping three halo planes (34 x 10) of (DT2, label) pairs
+// in shared memory; outside the array the halo holds (0, 0), which never
+// matches an object label. Per plane, the labelled foreground voxels are
+// compacted to the front of the CTA so that the 26-neighbour (8 in 2D) test
+// runs on full warps; every neighbour is evaluated without early exit.
+// Kept centres collect in shared memory and leave with one global atomic
+// per list every kRidgeFlush planes: centres painted from crescent tables
+// (3D, r^2 <= kCresT, with a dominant neighbour; every 2D centre) go to the
+// front of `surv`, the others (painted row by row) to the back.
 // Record: x = linear index, y = r^2 | dominant neighbour code << 25 (code =
 // (dz+1)*9 + (dy+1)*3 + (dx+1), or 31 for none).
-constexpr int kRidgeRows = 8;
+constexpr int kTX = 32, kTY = 8;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kPlane = kHX * kHY;
+constexpr int kRidgeZ = 16, kRidgeFlush = 4;
 
 template <int NDIM>
 __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
-                                                       uint32_t* __restrict__ lt2,
-                                                       const uint32_t* __restrict__ mtab,
-                                                       uint32_t cap, Dims d, uint2* __restrict__ surv,
+                                                       uint32_t* __restrict__ lt2, Dims d,
+                                                       uint2* __restrict__ surv,
                                                        WsHeader* __restrict__ hdr) {
-  __shared__ uint2 buf[256 * kRidgeRows];
-  __shared__ uint32_t cnt, base, flags;
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    cnt = 0;
+  __shared__ uint2 sDL[3][kPlane];
+  __shared__ uint2 bufA[256 * kRidgeFlush], bufB[256 * kRidgeFlush];
+  __shared__ uint16_t work[256];
+  __shared__ uint32_t wcnt[8];
+  __shared__ uint32_t cntA, cntB, baseA, baseB, flags;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int z0 = NDIM == 3 ? blockIdx.z * kRidgeZ : 0;
+  const int z1 = NDIM == 3 ? min(d.nz, z0 + kRidgeZ) : 1;
+  const size_t plane = (size_t)d.nx * d.ny;
+  const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
+  const unsigned below = (1u << lane) - 1u;
+  if (tid == 0) {
+    cntA = cntB = 0;
     flags = 0;
   }
-  __syncthreads();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int z = blockIdx.z;
-  const bool in = x < d.nx;
-  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
-  for (int r = 0; r < kRidgeRows; ++r) {
-    const int y = blockIdx.y * kRidgeRows + r;
-    if (y >= d.ny) break;  // uniform across the CTA
-    const uint32_t v = in ? (uint32_t)(z * sz + y * sy + x) : 0u;
-    bool keep = false, touch = false, bad = false;
-    uint32_t r2 = 0, code = kNoDominant;
-    if (in) {
-      r2 = dt2[v];
-      const uint32_t l = labels[v];
-      lt2[v] = 0u;
-      if (r2 == 0) {
-        bad = l != 0;
-      } else {
-        if (x + 1 < d.nx && dt2[v + 1] && labels[v + 1] != l) touch = true;
-        if (y + 1 < d.ny && dt2[v + sy] && labels[v + sy] != l) touch = true;
-        if (NDIM == 3 && z + 1 < d.nz && dt2[v + sz] && labels[v + sz] != l) touch = true;
-        if (l != 0) {
-          keep = true;
-          uint32_t m1 = UINT_MAX, m2 = UINT_MAX, m3 = UINT_MAX;
-          if (r2 <= cap) {
-            m1 = __ldg(mtab + r2);
-            m2 = __ldg(mtab + (cap + 1) + r2);
-            if (NDIM == 3) m3 = __ldg(mtab + 2 * (size_t)(cap + 1) + r2);
+  auto load_plane = [&](int z, int slot) {
+    for (int i = tid; i < kPlane; i += 256) {
+      const int hx = i % kHX, hy = i / kHX;
+      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+      uint2 dl = make_uint2(0u, 0u);
+      if (z >= 0 && z < d.nz && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
+        const size_t g = (size_t)z * plane + (size_t)gy * d.nx + gx;
+        dl = make_uint2(dt2[g], labels[g]);
+      }
+      sDL[slot][i] = dl;
+    }
+  };
+  if (NDIM == 3) {
+    load_plane(z0 - 1, (z0 + 2) % 3);
+    load_plane(z0, z0 % 3);
+  } else {
+    load_plane(-1, 2);
+    load_plane(0, 0);
+    load_plane(1, 1);
+  }
+  for (int z = z0; z < z1; ++z) {
+    if (NDIM == 3) load_plane(z + 1, (z + 1) % 3);
+    __syncthreads();
+    const int sm = NDIM == 3 ? (z + 2) % 3 : 2, s0 = NDIM == 3 ? z % 3 : 0, sp = NDIM == 3 ? (z + 1) % 3 : 1;
+    // pass 1, every voxel of the tile: clear LT2, flags, compaction
+    {
+      const int tx = tid & 31, ty = tid >> 5;
+      const int x = x0 + tx, y = y0 + ty;
+      const bool in = x < d.nx && y < d.ny;
+      const int c = (ty + 1) * kHX + (tx + 1);
+      const uint2 me = sDL[s0][c];
+      bool isw = false, touch = false, bad = false;
+      if (in) {
+        lt2[(size_t)z * plane + (size_t)y * d.nx + x] = 0u;
+        bad = me.x == 0 && me.y != 0;
+        if (me.x != 0) {
+          const uint2 ex = sDL[s0][c + 1], ey = sDL[s0][c + kHX];
+          touch = (ex.x && ex.y != me.y) || (ey.x && ey.y != me.y);
+          if (NDIM == 3) {
+            const uint2 ez = sDL[sp][c];
+            touch = touch || (ez.x && ez.y != me.y);
           }
-          float best_reach = -1e30f;
-          const int zlo = NDIM == 3 ? -1 : 0, zhi = NDIM == 3 ? 1 : 0;
-          for (int dz = zlo; dz <= zhi && keep; ++dz) {
-            if (z + dz < 0 || z + dz >= d.nz) continue;
-            for (int dy = -1; dy <= 1 && keep; ++dy) {
-              if (y + dy < 0 || y + dy >= d.ny) continue;
-              for (int dx = -1; dx <= 1; ++dx) {
-                if ((dx | dy | dz) == 0 || x + dx < 0 || x + dx >= d.nx) continue;
-                const uint32_t u = (uint32_t)((int64_t)v + dz * (int64_t)sz + dy * (int64_t)sy + dx);
-                if (labels[u] != l) continue;
-                const uint32_t rn = dt2[u];
-                const int cls = abs(dx) + abs(dy) + abs(dz);
-                const uint32_t mm = cls == 1 ? m1 : (cls == 2 ? m2 : m3);
-                if (rn >= mm) {
-                  keep = false;
-                  break;
-                }
-                if (rn > r2 || (rn == r2 && u > v)) {
-                  const float reach =
-                      sqrtf((float)rn) - (cls == 1 ? 1.0f : (cls == 2 ? 1.41421356f : 1.73205081f));
-                  if (reach > best_reach) {
-                    best_reach = reach;
-                    code = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-                  }
-                }
-              }
+        }
+        isw = me.x != 0 && me.y != 0;
+      }
+      if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
+      if (__any_sync(kFull, touch) && lane == 0) atomicOr(&flags, 2u);
+      const unsigned bal = __ballot_sync(kFull, isw);
+      if (lane == 0) wcnt[warp] = (uint32_t)__popc(bal);
+      __syncthreads();
+      uint32_t off = 0;
+      for (int w2 = 0; w2 < warp; ++w2) off += wcnt[w2];
+      if (isw) work[off + __popc(bal & below)] = (uint16_t)tid;
+    }
+    __syncthreads();
+    uint32_t nwork = 0;
+    for (int w2 = 0; w2 < 8; ++w2) nwork += wcnt[w2];
+    // pass 2, compacted labelled foreground voxels: containment test
+    bool keepA = false, keepB = false;
+    uint2 rec = make_uint2(0u, 0u);
+    if ((uint32_t)tid < nwork) {
+      const int t = work[tid];
+      const int tx = t & 31, ty = t >> 5;
+      const int c = (ty + 1) * kHX + (tx + 1);
+      const uint2 me = sDL[s0][c];
+      const uint32_t r2 = me.x, l = me.y;
+      int m[3] = {kNoTable, kNoTable, kNoTable};
+      if (r2 <= kMCap) {
+        m[0] = (int)mt[r2];
+        m[1] = (int)mt[(kMCap + 1) + r2];
+        if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
+      }
+      bool pruned = false;
+      int brn[3] = {-1, -1, -1};  // largest higher-ranked same-label r'^2 per class
+      uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
+#pragma unroll
+      for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
+        const int slot = dz < 0 ? sm : (dz == 0 ? s0 : sp);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            const uint2 nb = sDL[slot][c + dy * kHX + dx];
+            const int rn = (int)nb.x;
+            const int k = (dx != 0) + (dy != 0) + (dz != 0) - 1;
+            const bool pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+            const bool same = nb.y == l;
+            pruned = pruned || (same && rn >= m[k]);
+            const bool higher = rn > (int)r2 || (rn == (int)r2 && pos);
+            if (same && higher && rn > brn[k]) {
+              brn[k] = rn;
+              bcode[k] = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
             }
           }
         }
       }
+      if (!pruned) {
+        uint32_t code = kNoDominant;
+        if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
+          // the candidate whose crescent has the fewest voxels
+          uint32_t best = UINT_MAX;
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            if (brn[k] >= 0) {
+              const uint32_t cb = cres_combo(k, r2, (uint32_t)brn[k]);
+              const uint32_t sz = g_cres_start[cb + 1] - g_cres_start[cb];
+              if (sz < best) {
+                best = sz;
+                code = bcode[k];
+              }
+            }
+        } else {
+          // the candidate whose ball comes closest to containing c's
+          int best = INT_MIN;
+#pragma unroll
+          for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
+            if (brn[k] >= 0 && brn[k] - m[k] > best) {
+              best = brn[k] - m[k];
+              code = bcode[k];
+            }
+        }
+        const uint32_t v = (uint32_t)((size_t)z * plane + (size_t)(y0 + ty) * d.nx + (x0 + tx));
+        rec = make_uint2(v, r2 | (code << 25));
+        const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
+        keepA = tab;
+        keepB = !tab;
+      }
     }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
-    if (__any_sync(kFull, touch) && lane == 0) atomicOr(&flags, 2u);
-    const unsigned bal = __ballot_sync(kFull, keep);
-    if (bal) {
+    const unsigned ba = __ballot_sync(kFull, keepA), bb = __ballot_sync(kFull, keepB);
+    if (ba) {
       uint32_t wb = 0;
-      if (lane == 0) wb = atomicAdd(&cnt, (uint32_t)__popc(bal));
+      if (lane == 0) wb = atomicAdd(&cntA, (uint32_t)__popc(ba));
       wb = __shfl_sync(kFull, wb, 0);
-      if (keep) buf[wb + __popc(bal & ((1u << lane) - 1u))] = make_uint2(v, r2 | (code << 25));
+      if (keepA) bufA[wb + __popc(ba & below)] = rec;
+    }
+    if (bb) {
+      uint32_t wb = 0;
+      if (lane == 0) wb = atomicAdd(&cntB, (uint32_t)__popc(bb));
+      wb = __shfl_sync(kFull, wb, 0);
+      if (keepB) bufB[wb + __popc(bb & below)] = rec;
+    }
+    __syncthreads();  // plane z-1 is free again; the buffers may be flushed
+    if ((z - z0) % kRidgeFlush == kRidgeFlush - 1 || z + 1 == z1) {
+      if (tid == 0) {
+        baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
+        baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
+      }
+      __syncthreads();
+      for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = bufA[i];
+      for (uint32_t i = tid; i < cntB; i += 256) surv[(size_t)d.n - 1 - (baseB + i)] = bufB[i];
+      __syncthreads();
+      if (tid == 0) cntA = cntB = 0;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    base = cnt ? atomicAdd(&hdr->n_surv, cnt) : 0u;
+  if (tid == 0) {
     if (flags & 1u) atomicOr(&hdr->error, ERR_LABEL_OUTSIDE_MASK);
     if (flags & 2u) atomicOr(&hdr->touch, 1u);
   }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) surv[base + i] = buf[i];
 }
 
+// ---------------------------------------------------------- paint kernel
 struct Centre {
   int cx, cy, cz, R;
-  uint32_t r2, label;
+  uint32_t r2, label, idx;
   int ddx, ddy, ddz, r2d;  // dominant neighbour offset and its r^2 (-1: none)
-  int start, pad;
+  int start, nseg;         // first item of this centre in the chunk; dy segments
+  float inv_nseg;
+  uint32_t vstart;  // table mode: first crescent voxel
+  int mode;         // 0 rows; 1 table; 3 table, ball inside the array
+  int S[3];         // linear stride of canonical axes x, y, z
+  uint32_t axes;    // world axis (2 bits each) and sign bit of canonical x, y, z
 };
+constexpr int kRowSeg = 8;  // rows per row-mode work item
 
-// Paints the part of one ball row (offsets dz, dy from the centre, squared
-// half-width h) that lies outside the dominant neighbour's ball.
-__device__ __forceinline__ void paint_row(const Centre& c, int dz, int dy, int h, size_t rowbase,
-                                          int nx, bool touch, const uint32_t* __restrict__ dt2,
-                                          const uint32_t* __restrict__ labels,
-                                          uint32_t* __restrict__ lt2) {
-  const int w = (int)isqrt24((uint32_t)h);
-  int hd = -1;
-  if (c.r2d >= 0) hd = c.r2d - (dz - c.ddz) * (dz - c.ddz) - (dy - c.ddy) * (dy - c.ddy);
-  auto vox = [&](int dx) {
-    const int x = c.cx + dx;
-    if (x < 0 || x >= nx) return;
-    const size_t i = rowbase + x;
-    if (dx * dx == h && dt2[i] == 0) return;  // ball boundary point may be background
-    if (touch && labels[i] != c.label) return;
+// Raises LT2 to c.r2 on row voxels dx in [a, b] (already clamped to the
+// array). Only the two ends of an exact row (w^2 == h) can be background.
+__device__ __forceinline__ void paint_span(const Centre& c, int a, int b, int w, bool exact,
+                                           size_t rowbase, bool touch,
+                                           const uint32_t* __restrict__ dt2,
+                                           const uint32_t* __restrict__ labels,
+                                           uint32_t* __restrict__ lt2) {
+  for (int dx = a; dx <= b; ++dx) {
+    const size_t i = rowbase + (size_t)(c.cx + dx);
+    if (exact && (dx == w || dx == -w) && dt2[i] == 0) continue;
+    if (touch && labels[i] != c.label) continue;
     atomicMax(lt2 + i, c.r2);
-  };
-  int xl = -w;
-  while (xl <= w && (hd < 0 || (xl - c.ddx) * (xl - c.ddx) > hd)) vox(xl++);
-  int xr = w;
-  while (xr >= xl && (hd < 0 || (xr - c.ddx) * (xr - c.ddx) > hd)) vox(xr--);
+  }
 }
 
-// Warps take chunks of 32 kept centres from a global counter. Each centre
-// contributes 2R+1 items (one per z offset in 3D, one per row in 2D); the 32
-// lanes share the items of the chunk, so big and small balls balance.
+// Row mode: rows dy0..dy0+7 of the disc at height dz, minus the dominant
+// neighbour's rows; half-widths are updated incrementally along the segment.
+__device__ __forceinline__ void paint_rows(const Centre& c, int dz, int seg, const Dims& d, size_t sy,
+                                           size_t sz, bool touch, const uint32_t* __restrict__ dt2,
+                                           const uint32_t* __restrict__ labels,
+                                           uint32_t* __restrict__ lt2) {
+  const int z = c.cz + dz;
+  if (z < 0 || z >= d.nz) return;
+  const int hz2 = (int)c.r2 - dz * dz;
+  const int dy0 = -c.R + seg * kRowSeg, dy1 = min(c.R, dy0 + kRowSeg - 1);
+  const int xmin = -c.cx, xmax = d.nx - 1 - c.cx;
+  int wr = -1, wd = -1;
+  for (int dy = dy0; dy <= dy1; ++dy) {
+    const int h = hz2 - dy * dy;
+    const int y = c.cy + dy;
+    if (h < 0 || y < 0 || y >= d.ny) continue;
+    if (wr < 0) wr = (int)isqrt24((uint32_t)h);
+    while (wr * wr > h) --wr;
+    while ((wr + 1) * (wr + 1) <= h) ++wr;
+    int hi1 = wr, lo2 = 1, hi2 = 0;  // pieces [-wr, hi1] and [lo2, hi2]
+    if (c.r2d >= 0) {
+      const int hd = c.r2d - (dz - c.ddz) * (dz - c.ddz) - (dy - c.ddy) * (dy - c.ddy);
+      if (hd >= 0) {
+        if (wd < 0) wd = (int)isqrt24((uint32_t)hd);
+        while (wd * wd > hd) --wd;
+        while ((wd + 1) * (wd + 1) <= hd) ++wd;
+        hi1 = min(wr, c.ddx - wd - 1);
+        lo2 = max(-wr, c.ddx + wd + 1);
+        hi2 = wr;
+      }
+    }
+    const bool exact = wr * wr == h;
+    const size_t rowbase = (size_t)z * sz + (size_t)y * sy;
+    paint_span(c, max(-wr, xmin), min(hi1, xmax), wr, exact, rowbase, touch, dt2, labels, lt2);
+    paint_span(c, max(lo2, xmin), min(hi2, xmax), wr, exact, rowbase, touch, dt2, labels, lt2);
+  }
+}
+
+// Table mode: crescent voxel t of the centre, mapped from the canonical frame.
+__device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, const Dims& d, bool touch,
+                                                  const uint32_t* __restrict__ dt2,
+                                                  const uint32_t* __restrict__ labels,
+                                                  uint32_t* __restrict__ lt2) {
+  const uint32_t p = g_cres_vox[c.vstart + t];
+  const int o0 = (int)(p & 0xFFu) - 128, o1 = (int)((p >> 8) & 0xFFu) - 128,
+            o2 = (int)((p >> 16) & 0xFFu) - 128;
+  if (!(c.mode & 2)) {  // ball may leave the array: check each coordinate
+    const int a0 = c.axes & 3, a1 = (c.axes >> 2) & 3, a2 = (c.axes >> 4) & 3;
+    const int v0 = (c.axes >> 6) & 1 ? -o0 : o0, v1 = (c.axes >> 7) & 1 ? -o1 : o1,
+              v2 = (c.axes >> 8) & 1 ? -o2 : o2;
+    const int x = c.cx + (a0 == 0 ? v0 : 0) + (a1 == 0 ? v1 : 0) + (a2 == 0 ? v2 : 0);
+    const int y = c.cy + (a0 == 1 ? v0 : 0) + (a1 == 1 ? v1 : 0) + (a2 == 1 ? v2 : 0);
+    const int z = c.cz + (a0 == 2 ? v0 : 0) + (a1 == 2 ? v1 : 0) + (a2 == 2 ? v2 : 0);
+    if (x < 0 || x >= d.nx || y < 0 || y >= d.ny || z < 0 || z >= d.nz) return;
+  }
+  const size_t i = (size_t)((int64_t)c.idx + (int64_t)o0 * c.S[0] + (int64_t)o1 * c.S[1] +
+                            (int64_t)o2 * c.S[2]);
+  if ((p >> 24) && dt2[i] == 0) return;
+  if (touch && labels[i] != c.label) return;
+  atomicMax(lt2 + i, c.r2);
+}
+
+// Decodes a centre record; returns its number of work items: crescent voxels
+// in table mode, (2R+1) * ceil((2R+1)/8) row segments in 3D row mode and
+// ceil((2R+1)/8) in 2D.
+template <int NDIM>
+__device__ __forceinline__ int make_centre(uint2 rec, bool table, const Dims& d, size_t sy, size_t sz,
+                                           bool touch, const uint32_t* __restrict__ dt2,
+                                           const uint32_t* __restrict__ labels, Centre& c) {
+  const uint32_t idx = rec.x, code = rec.y >> 25;
+  c.idx = idx;
+  c.r2 = rec.y & 0x1FFFFFFu;
+  c.cx = (int)(idx % (uint32_t)d.nx);
+  const uint32_t t = idx / (uint32_t)d.nx;
+  c.cy = (int)(t % (uint32_t)d.ny);
+  c.cz = (int)(t / (uint32_t)d.ny);
+  c.R = (int)isqrt24(c.r2);
+  c.label = touch ? labels[idx] : 0u;
+  c.mode = 0;
+  c.vstart = 0;
+  c.axes = 0;
+  c.S[0] = c.S[1] = c.S[2] = 0;
+  c.start = 0;
+  if (code != kNoDominant) {
+    c.ddz = (int)(code / 9) - 1;
+    c.ddy = (int)(code / 3 % 3) - 1;
+    c.ddx = (int)(code % 3) - 1;
+    c.r2d = (int)dt2[(int64_t)idx + c.ddz * (int64_t)sz + c.ddy * (int64_t)sy + c.ddx];
+  } else {
+    c.ddx = c.ddy = c.ddz = 0;
+    c.r2d = -1;
+  }
+  c.nseg = (2 * c.R + kRowSeg) / kRowSeg;
+  c.inv_nseg = 1.0f / (float)c.nseg;
+  if (NDIM == 3 && table) {
+    // canonical x, y, z -> the nonzero axes of the offset first (in x, y,
+    // z order), then the zero axes
+    const int cls = (c.ddx != 0) + (c.ddy != 0) + (c.ddz != 0);
+    int a0 = 0, a1 = 1, a2 = 2;
+    if (cls == 2) {
+      if (c.ddx == 0) { a0 = 1; a1 = 2; a2 = 0; }
+      else if (c.ddy == 0) { a0 = 0; a1 = 2; a2 = 1; }
+    } else if (cls == 1) {
+      if (c.ddy != 0) { a0 = 1; a1 = 0; a2 = 2; }
+      else if (c.ddz != 0) { a0 = 2; a1 = 0; a2 = 1; }
+    }
+    auto comp = [&](int a) { return a == 0 ? c.ddx : (a == 1 ? c.ddy : c.ddz); };
+    auto stride = [&](int a) { return a == 0 ? 1LL : (a == 1 ? (long long)sy : (long long)sz); };
+    const int g0 = comp(a0) < 0, g1 = comp(a1) < 0, g2 = comp(a2) < 0;
+    c.axes = (uint32_t)(a0 | (a1 << 2) | (a2 << 4) | (g0 << 6) | (g1 << 7) | (g2 << 8));
+    c.S[0] = (int)(g0 ? -stride(a0) : stride(a0));
+    c.S[1] = (int)(g1 ? -stride(a1) : stride(a1));
+    c.S[2] = (int)(g2 ? -stride(a2) : stride(a2));
+    const uint32_t cb = cres_combo(cls - 1, c.r2, (uint32_t)c.r2d);
+    c.vstart = g_cres_start[cb];
+    const bool inside = c.cx - c.R >= 0 && c.cx + c.R < d.nx && c.cy - c.R >= 0 && c.cy + c.R < d.ny &&
+                        c.cz - c.R >= 0 && c.cz + c.R < d.nz;
+    c.mode = inside ? 3 : 1;
+    return (int)(g_cres_start[cb + 1] - c.vstart);
+  }
+  return (NDIM == 3 ? 2 * c.R + 1 : 1) * c.nseg;
+}
+
+// Row-mode item `local` of a centre: the z offset and the group of 8 rows.
+template <int NDIM>
+__device__ __forceinline__ void paint_row_item(const Centre& c, int local, const Dims& d, size_t sy,
+                                               size_t sz, bool touch, const uint32_t* __restrict__ dt2,
+                                               const uint32_t* __restrict__ labels,
+                                               uint32_t* __restrict__ lt2) {
+  if (NDIM == 3) {
+    int q = (int)((float)local * c.inv_nseg);
+    if (q * c.nseg > local) --q;
+    else if ((q + 1) * c.nseg <= local) ++q;
+    paint_rows(c, q - c.R, local - q * c.nseg, d, sy, sz, touch, dt2, labels, lt2);
+  } else {
+    paint_rows(c, 0, local, d, sy, sz, touch, dt2, labels, lt2);
+  }
+}
+
+// Two phases, each fed by a global work counter.
+// 1. (3D) Row-mode centres from the back of the list, one per warp: the
+//    lanes share its (2R+1) * ceil((2R+1)/8) row segments. These are the
+//    biggest balls, so they go first.
+// 2. Chunks of 32 centres from the front of the list: the 32 lanes share the
+//    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
+//    and small crescents balance.
 template <int NDIM>
 __global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__ surv,
                                                        const uint32_t* __restrict__ dt2,
@@ -240,41 +555,32 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__
   __shared__ Centre cs[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t n = *(volatile uint32_t*)&hdr->n_surv;
+  const uint32_t nbig = *(volatile uint32_t*)&hdr->n_big;
   const bool touch = *(volatile uint32_t*)&hdr->touch != 0;
-  const uint32_t nchunks = (n + 31) / 32;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
-  uint32_t* counter = &hdr->reserved[0];
+  if (NDIM == 3) {
+    for (;;) {
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(&hdr->ctr_big, 1u);
+      b = __shfl_sync(kFull, b, 0);
+      if (b >= nbig) break;
+      Centre c;
+      const int items = make_centre<NDIM>(surv[(size_t)d.n - 1 - b], false, d, sy, sz, touch, dt2, labels, c);
+      for (int k = lane; k < items; k += 32) paint_row_item<NDIM>(c, k, d, sy, sz, touch, dt2, labels, lt2);
+    }
+  }
+  const uint32_t nchunks = (n + 31) / 32;
   for (;;) {
     uint32_t ch = 0;
-    if (lane == 0) ch = atomicAdd(counter, 1u);
+    if (lane == 0) ch = atomicAdd(&hdr->ctr_small, 1u);
     ch = __shfl_sync(kFull, ch, 0);
     if (ch >= nchunks) break;
     const uint32_t i = ch * 32 + lane;
     int cnt = 0;
     if (i < n) {
-      const uint2 rec = surv[i];
-      const uint32_t idx = rec.x, code = rec.y >> 25;
       Centre c;
-      c.r2 = rec.y & 0x1FFFFFFu;
-      c.cx = (int)(idx % (uint32_t)d.nx);
-      const uint32_t t = idx / (uint32_t)d.nx;
-      c.cy = (int)(t % (uint32_t)d.ny);
-      c.cz = (int)(t / (uint32_t)d.ny);
-      c.R = (int)isqrt24(c.r2);
-      c.label = touch ? labels[idx] : 0u;
-      if (code != kNoDominant) {
-        c.ddz = (int)(code / 9) - 1;
-        c.ddy = (int)(code / 3 % 3) - 1;
-        c.ddx = (int)(code % 3) - 1;
-        c.r2d = (int)dt2[(int64_t)idx + c.ddz * (int64_t)sz + c.ddy * (int64_t)sy + c.ddx];
-      } else {
-        c.ddx = c.ddy = c.ddz = 0;
-        c.r2d = -1;
-      }
-      c.start = 0;
-      c.pad = 0;
+      cnt = make_centre<NDIM>(surv[i], true, d, sy, sz, touch, dt2, labels, c);
       cs[w][lane] = c;
-      cnt = 2 * c.R + 1;
     }
     int incl = cnt;
 #pragma unroll
@@ -294,27 +600,13 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__
         const int s = __shfl_sync(kFull, start, j + step);
         if (s <= k) j += step;
       }
-      if (k < total) {
-        const Centre c = cs[w][j];
-        const int u = k - c.start - c.R;
-        if (NDIM == 3) {
-          const int z = c.cz + u;
-          if (z >= 0 && z < d.nz) {
-            const int hz2 = (int)c.r2 - u * u;
-            const int hz = (int)isqrt24((uint32_t)hz2);
-            for (int dy = -hz; dy <= hz; ++dy) {
-              const int y = c.cy + dy;
-              if (y < 0 || y >= d.ny) continue;
-              paint_row(c, u, dy, hz2 - dy * dy, (size_t)z * sz + (size_t)y * sy, d.nx, touch, dt2,
-                        labels, lt2);
-            }
-          }
-        } else {
-          const int y = c.cy + u;
-          if (y >= 0 && y < d.ny)
-            paint_row(c, 0, u, (int)c.r2 - u * u, (size_t)y * sy, d.nx, touch, dt2, labels, lt2);
-        }
-      }
+      if (k >= total) continue;
+      const Centre& c = cs[w][j];
+      const int local = k - c.start;
+      if (c.mode)
+        paint_table_voxel(c, (uint32_t)local, d, touch, dt2, labels, lt2);
+      else
+        paint_row_item<NDIM>(c, local, d, sy, sz, touch, dt2, labels, lt2);
     }
     __syncwarp();
   }
@@ -322,48 +614,21 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__
 
 }  // namespace
 
-uint32_t lt_table_r2cap(const Dims& d) {
-  int m = std::min((d.nx + 1) / 2, (d.ny + 1) / 2);
-  if (d.ndim == 3) m = std::min(m, (d.nz + 1) / 2);
-  const uint64_t bound = (uint64_t)m * (uint64_t)m;
-  return (uint32_t)(bound < kTableCap ? bound : kTableCap);
-}
-
-static size_t table_bytes(const Dims& d) {
-  const int ncls = d.ndim == 3 ? 3 : 2;
-  return align_up((size_t)ncls * (lt_table_r2cap(d) + 1) * sizeof(uint32_t));
-}
-
-size_t lt_workspace_bytes(const Dims& d) { return table_bytes(d) + align_up((size_t)d.n * sizeof(uint2)); }
+size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint2)); }
 
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s) {
-  const uint32_t cap = lt_table_r2cap(d);
-  const int ncls = d.ndim == 3 ? 3 : 2;
-  uint32_t* tab = reinterpret_cast<uint32_t*>(body);
-  uint2* surv = reinterpret_cast<uint2*>(reinterpret_cast<char*>(body) + table_bytes(d));
-  cudaError_t e = cudaMemsetAsync(tab, 0, (size_t)ncls * (cap + 1) * sizeof(uint32_t), s);
+  cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
-  int R = 0;
-  while ((uint32_t)(R + 1) * (uint32_t)(R + 1) <= cap) ++R;
-  const size_t pairs = (size_t)(R + 1) * (R + 1);
-  const size_t want = (pairs + 255) / 256, cap_blocks = (size_t)sm_count() * 8;
-  const unsigned tblocks = (unsigned)(want < cap_blocks ? want : cap_blocks);
-  {
-    TraceScope t("lt_table_points", s);
-    mtable_points_kernel<<<tblocks, 256, 0, s>>>(tab, cap, R, d.ndim);
-  }
-  {
-    TraceScope t("lt_table_prefix", s);
-    mtable_prefix_kernel<<<ncls, 1024, 0, s>>>(tab, cap);
-  }
-  dim3 grid((d.nx + 255) / 256, (d.ny + kRidgeRows - 1) / kRidgeRows, d.nz);
+  uint2* surv = reinterpret_cast<uint2*>(body);
+  dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY,
+            d.ndim == 3 ? (d.nz + kRidgeZ - 1) / kRidgeZ : 1);
   {
     TraceScope t("lt_ridge", s);
     if (d.ndim == 3)
-      lt_ridge_kernel<3><<<grid, 256, 0, s>>>(dt2, labels, lt2, tab, cap, d, surv, hdr);
+      lt_ridge_kernel<3><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
     else
-      lt_ridge_kernel<2><<<grid, 256, 0, s>>>(dt2, labels, lt2, tab, cap, d, surv, hdr);
+      lt_ridge_kernel<2><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -21,8 +21,10 @@ struct Dims {
 struct WsHeader {
   uint32_t error;   // bit set of ERR_* found on the device
   uint32_t touch;   // nonzero: two face-adjacent foreground voxels differ in label
-  uint32_t n_surv;  // number of centres kept by the ridge kernel
-  uint32_t reserved[61];
+  uint32_t n_surv;  // kept centres painted from crescent tables (list from the front)
+  uint32_t n_big;   // kept centres painted row by row (list from the back)
+  uint32_t ctr_small, ctr_big;  // work counters of the paint kernel
+  uint32_t reserved[58];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -55,7 +57,6 @@ size_t edt_workspace_bytes(const Dims& d);
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
                        cudaStream_t s);
 // lt.cu
-uint32_t lt_table_r2cap(const Dims& d);
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s);
