@@ -112,8 +112,10 @@ lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64
  * its ball that one chosen higher-ranked neighbour's ball does not hold.
  * Neither step changes the maximum (proof in the kernel source).
  * Device-detected error: LT_ERR_LABEL_OUTSIDE_MASK.
- * Workspace: lt_local_thickness_workspace_size bytes (8 bytes per voxel for
- * the centre list plus a lookup table of at most 3 MiB). */
+ * Workspace: lt_local_thickness_workspace_size bytes (16 bytes per voxel for
+ * the centre list). The first call on a device also copies lookup tables
+ * (about 13 MiB, built once per process on the host) into device memory
+ * owned by the library; make that first call before any stream capture. */
 size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
 lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, int ndim,
                              int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,

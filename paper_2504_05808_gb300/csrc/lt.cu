@@ -183,23 +183,23 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // (3D, r^2 <= kCresT, with a dominant neighbour; every 2D centre) go to the
 // front of `surv`, the others (painted row by row) to the back.
 // Record: x = linear index, y = r^2 | dominant neighbour code << 25 (code =
-// (dz+1)*9 + (dy+1)*3 + (dx+1), or 31 for none).
+// (dz+1)*9 + (dy+1)*3 + (dx+1), or 31 for none), z = codes of up to two
+// more higher-ranked same-label neighbours (5 bits each, 31 for none).
 constexpr int kTX = 32, kTY = 8;
 constexpr int kHX = kTX + 2, kHY = kTY + 2, kPlane = kHX * kHY;
-constexpr int kRidgeZ = 16, kRidgeFlush = 4;
+constexpr int kRidgeZ = 16, kRidgeFlush = 2;
 
 template <int NDIM>
 __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
-                                                       uint2* __restrict__ surv,
+                                                       uint4* __restrict__ surv,
                                                        WsHeader* __restrict__ hdr) {
   __shared__ uint2 sDL[3][kPlane];
-  __shared__ uint2 bufA[256 * kRidgeFlush], bufB[256 * kRidgeFlush];
+  __shared__ uint4 bufA[256 * kRidgeFlush], bufB[256 * kRidgeFlush];
   __shared__ uint16_t work[256];
-  __shared__ uint32_t wcnt[8];
-  __shared__ uint32_t cntA, cntB, baseA, baseB, flags;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int z0 = NDIM == 3 ? blockIdx.z * kRidgeZ : 0;
   const int z1 = NDIM == 3 ? min(d.nz, z0 + kRidgeZ) : 1;
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
   if (tid == 0) {
     cntA = cntB = 0;
     flags = 0;
+    nwork_s = 0;
   }
   auto load_plane = [&](int z, int slot) {
     for (int i = tid; i < kPlane; i += 256) {
@@ -258,18 +259,16 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
       if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
       if (__any_sync(kFull, touch) && lane == 0) atomicOr(&flags, 2u);
       const unsigned bal = __ballot_sync(kFull, isw);
-      if (lane == 0) wcnt[warp] = (uint32_t)__popc(bal);
-      __syncthreads();
       uint32_t off = 0;
-      for (int w2 = 0; w2 < warp; ++w2) off += wcnt[w2];
+      if (lane == 0 && bal) off = atomicAdd(&nwork_s, (uint32_t)__popc(bal));
+      off = __shfl_sync(kFull, off, 0);
       if (isw) work[off + __popc(bal & below)] = (uint16_t)tid;
     }
     __syncthreads();
-    uint32_t nwork = 0;
-    for (int w2 = 0; w2 < 8; ++w2) nwork += wcnt[w2];
+    const uint32_t nwork = nwork_s;
     // pass 2, compacted labelled foreground voxels: containment test
     bool keepA = false, keepB = false;
-    uint2 rec = make_uint2(0u, 0u);
+    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
     if ((uint32_t)tid < nwork) {
       const int t = work[tid];
       const int tx = t & 31, ty = t >> 5;
@@ -282,9 +281,10 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
         m[1] = (int)mt[(kMCap + 1) + r2];
         if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
       }
-      bool pruned = false;
-      int brn[3] = {-1, -1, -1};  // largest higher-ranked same-label r'^2 per class
-      uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
+      // per class, the largest key (r'^2 << 6 | rank bit << 5 | offset code)
+      // over same-label neighbours: its r'^2 decides containment, and it is
+      // the candidate dominant when it ranks above c (2 r'^2 + bit > 2 r^2)
+      uint32_t kmax[3] = {0u, 0u, 0u};
 #pragma unroll
       for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
         const int slot = dz < 0 ? sm : (dz == 0 ? s0 : sp);
@@ -294,21 +294,27 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
           for (int dx = -1; dx <= 1; ++dx) {
             if (dx == 0 && dy == 0 && dz == 0) continue;
             const uint2 nb = sDL[slot][c + dy * kHX + dx];
-            const int rn = (int)nb.x;
             const int k = (dx != 0) + (dy != 0) + (dz != 0) - 1;
-            const bool pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-            const bool same = nb.y == l;
-            pruned = pruned || (same && rn >= m[k]);
-            const bool higher = rn > (int)r2 || (rn == (int)r2 && pos);
-            if (same && higher && rn > brn[k]) {
-              brn[k] = rn;
-              bcode[k] = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-            }
+            const uint32_t pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+            const uint32_t key = (nb.x << 6) | (pos << 5) | (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+            kmax[k] = max(kmax[k], nb.y == l ? key : 0u);
           }
+        }
+      }
+      bool pruned = false;
+      int brn[3] = {-1, -1, -1};
+      uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
+#pragma unroll
+      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k) {
+        pruned = pruned || (int)(kmax[k] >> 6) >= m[k];
+        if ((kmax[k] >> 5) > 2 * r2) {
+          brn[k] = (int)(kmax[k] >> 6);
+          bcode[k] = kmax[k] & 31u;
         }
       }
       if (!pruned) {
         uint32_t code = kNoDominant;
+        int kd = -1;
         if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
           // the candidate whose crescent has the fewest voxels
           uint32_t best = UINT_MAX;
@@ -320,6 +326,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
               if (sz < best) {
                 best = sz;
                 code = bcode[k];
+                kd = k;
               }
             }
         } else {
@@ -333,7 +340,15 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
             }
         }
         const uint32_t v = (uint32_t)((size_t)z * plane + (size_t)(y0 + ty) * d.nx + (x0 + tx));
-        rec = make_uint2(v, r2 | (code << 25));
+        // the other classes' candidates: extra balls a crescent voxel may lie in
+        uint32_t extra = kNoDominant | (kNoDominant << 5), ne = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (NDIM == 3 && k != kd && brn[k] >= 0 && ne < 2) {
+            extra = (extra & ~(31u << (5 * ne))) | (bcode[k] << (5 * ne));
+            ++ne;
+          }
+        rec = make_uint4(v, r2 | (code << 25), extra, 0u);
         const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
         keepA = tab;
         keepB = !tab;
@@ -353,6 +368,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
       if (keepB) bufB[wb + __popc(bb & below)] = rec;
     }
     __syncthreads();  // plane z-1 is free again; the buffers may be flushed
+    if (tid == 0) nwork_s = 0;
     if ((z - z0) % kRidgeFlush == kRidgeFlush - 1 || z + 1 == z1) {
       if (tid == 0) {
         baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
@@ -382,6 +398,8 @@ struct Centre {
   int mode;         // 0 rows; 1 table; 3 table, ball inside the array
   int S[3];         // linear stride of canonical axes x, y, z
   uint32_t axes;    // world axis (2 bits each) and sign bit of canonical x, y, z
+  int eoff[2];      // extra higher-ranked balls: canonical offset, 2 bits per axis
+  int er2[2];       // and their r^2 (-1: none)
 };
 constexpr int kRowSeg = 8;  // rows per row-mode work item
 
@@ -446,6 +464,12 @@ __device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, c
   const uint32_t p = g_cres_vox[c.vstart + t];
   const int o0 = (int)(p & 0xFFu) - 128, o1 = (int)((p >> 8) & 0xFFu) - 128,
             o2 = (int)((p >> 16) & 0xFFu) - 128;
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (c.er2[q] >= 0) {  // inside another higher-ranked same-label ball: covered there
+      const int e0 = (c.eoff[q] & 3) - 1, e1 = ((c.eoff[q] >> 2) & 3) - 1, e2 = ((c.eoff[q] >> 4) & 3) - 1;
+      if ((o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= c.er2[q]) return;
+    }
   if (!(c.mode & 2)) {  // ball may leave the array: check each coordinate
     const int a0 = c.axes & 3, a1 = (c.axes >> 2) & 3, a2 = (c.axes >> 4) & 3;
     const int v0 = (c.axes >> 6) & 1 ? -o0 : o0, v1 = (c.axes >> 7) & 1 ? -o1 : o1,
@@ -466,7 +490,7 @@ __device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, c
 // in table mode, (2R+1) * ceil((2R+1)/8) row segments in 3D row mode and
 // ceil((2R+1)/8) in 2D.
 template <int NDIM>
-__device__ __forceinline__ int make_centre(uint2 rec, bool table, const Dims& d, size_t sy, size_t sz,
+__device__ __forceinline__ int make_centre(uint4 rec, bool table, const Dims& d, size_t sy, size_t sz,
                                            bool touch, const uint32_t* __restrict__ dt2,
                                            const uint32_t* __restrict__ labels, Centre& c) {
   const uint32_t idx = rec.x, code = rec.y >> 25;
@@ -483,6 +507,8 @@ __device__ __forceinline__ int make_centre(uint2 rec, bool table, const Dims& d,
   c.axes = 0;
   c.S[0] = c.S[1] = c.S[2] = 0;
   c.start = 0;
+  c.eoff[0] = c.eoff[1] = 0;
+  c.er2[0] = c.er2[1] = -1;
   if (code != kNoDominant) {
     c.ddz = (int)(code / 9) - 1;
     c.ddy = (int)(code / 3 % 3) - 1;
@@ -513,6 +539,17 @@ __device__ __forceinline__ int make_centre(uint2 rec, bool table, const Dims& d,
     c.S[0] = (int)(g0 ? -stride(a0) : stride(a0));
     c.S[1] = (int)(g1 ? -stride(a1) : stride(a1));
     c.S[2] = (int)(g2 ? -stride(a2) : stride(a2));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t ec = (rec.z >> (5 * q)) & 31u;
+      if (ec == kNoDominant) continue;
+      const int ez = (int)(ec / 9) - 1, ey = (int)(ec / 3 % 3) - 1, ex = (int)(ec % 3) - 1;
+      c.er2[q] = (int)dt2[(int64_t)idx + ez * (int64_t)sz + ey * (int64_t)sy + ex];
+      auto wcomp = [&](int a) { return a == 0 ? ex : (a == 1 ? ey : ez); };
+      const int q0 = g0 ? -wcomp(a0) : wcomp(a0), q1 = g1 ? -wcomp(a1) : wcomp(a1),
+                q2 = g2 ? -wcomp(a2) : wcomp(a2);
+      c.eoff[q] = (q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4);
+    }
     const uint32_t cb = cres_combo(cls - 1, c.r2, (uint32_t)c.r2d);
     c.vstart = g_cres_start[cb];
     const bool inside = c.cx - c.R >= 0 && c.cx + c.R < d.nx && c.cy - c.R >= 0 && c.cy + c.R < d.ny &&
@@ -547,7 +584,7 @@ __device__ __forceinline__ void paint_row_item(const Centre& c, int local, const
 //    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
 //    and small crescents balance.
 template <int NDIM>
-__global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__ surv,
+__global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__ surv,
                                                        const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
@@ -614,13 +651,13 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint2* __restrict__
 
 }  // namespace
 
-size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint2)); }
+size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint4)); }
 
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
-  uint2* surv = reinterpret_cast<uint2*>(body);
+  uint4* surv = reinterpret_cast<uint4*>(body);
   dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY,
             d.ndim == 3 ? (d.nz + kRidgeZ - 1) / kRidgeZ : 1);
   {

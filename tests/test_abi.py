@@ -47,9 +47,9 @@ def test_status_strings_and_version(lt):
 def test_workspace_sizes(lt):
     L = lt.lib
     n = 512 ** 3
-    # local thickness: header + lookup table + 8 bytes per voxel
+    # local thickness: header + 16 bytes per voxel (centre records)
     ws = L.lt_local_thickness_workspace_size(3, 512, 512, 512)
-    assert 8 * n < ws < 8 * n + (4 << 20)
+    assert 16 * n <= ws < 16 * n + 4096
     assert L.lt_edt_workspace_size(3, 512, 512, 512) == 0
     assert L.lt_edt_workspace_size(2, 100, 3000, 1) == 4 * 300000
     assert L.lt_shape_workspace_size(1000) >= 28 * 1000
