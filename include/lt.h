@@ -145,6 +145,57 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
                             float* sphericity, float* roundness, const lt_object_stats* stats,
                             void* stream);
 
+/* ------------------------------------------------ learned sphericity --
+ * A correction of S_LT toward the strict (mesh) sphericity of Eq. 1 by a
+ * small network; the paper has none, so its definition is this library's:
+ *
+ * lt_object_features: 48 features per object into `features`
+ *   ([n_labels][48] float, device), from labels, lt2, the per-object sums of
+ *   lt_shape_measures (`stats`, all five arrays required) and its outputs
+ *   S_LT and R_LT. Index: 0 log(V)/10, 1 log(n_shell)/10, 2 log(M)/4 with
+ *   M = sqrt(max LT2), 3 (mean LT)/M, 4 R_LT, 5 S_LT, 6-21 the fraction of
+ *   interior (non-shell) voxels whose LT/M falls in bin b (the largest b in
+ *   0..15 with b^2 * max LT2 <= 256 * LT2), 22-37 the same over the shell,
+ *   38-47 zero. Rows of empty labels (and label 0) are zero. One extra pass
+ *   over the volume. Workspace: lt_features_workspace_size (128 bytes per
+ *   label + 256).
+ * Network: 48 -> 64 -> 64 -> 1 with ReLU, parameters in one FP32 vector of
+ *   LT_MLP_PARAMS floats laid out W1[48][64], b1[64], W2[64][64], b2[64],
+ *   w3[64], b3 (W[i][j]: input i to output j). Inputs, weights and hidden
+ *   activations are rounded to BF16; sums run in FP32.
+ * lt_mlp_infer: s_learned[o] = clamp(sphericity[o] + net(features[o]), 0, 1)
+ *   for o < n (NaN where sphericity is NaN). Device pointers.
+ * lt_mlp_gradients: for the batch batch_idx[0..batch), the gradient (device,
+ *   LT_MLP_PARAMS floats) of the mean over the batch of
+ *   (sphericity + net(features) - target)^2 with respect to the FP32
+ *   parameters (straight through the BF16 roundings), and the loss (device
+ *   float, may be NULL). The sum over the batch runs in a fixed order, so
+ *   the result is deterministic. Workspace: lt_mlp_train_workspace_size.
+ * lt_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ *   corrected; `step` counts from 1) on params with moments m and v.
+ * lt_mlp_train_step: lt_mlp_gradients then lt_mlp_adam; `grad` is scratch
+ *   of LT_MLP_PARAMS floats. */
+#define LT_MLP_FEATURES 48
+#define LT_MLP_HIDDEN 64
+#define LT_MLP_PARAMS 7361
+size_t lt_features_workspace_size(uint32_t n_labels);
+lt_status lt_object_features(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, int ndim,
+                             int64_t nx, int64_t ny, int64_t nz, const lt_object_stats* stats,
+                             const float* sphericity, const float* roundness, void* ws, size_t ws_bytes,
+                             float* features, void* stream);
+lt_status lt_mlp_infer(const float* params, const float* features, const float* sphericity, uint32_t n,
+                       float* s_learned, void* stream);
+size_t lt_mlp_train_workspace_size(uint32_t batch);
+lt_status lt_mlp_gradients(const float* params, const float* features, const float* sphericity,
+                           const float* target, const uint32_t* batch_idx, uint32_t batch, void* ws,
+                           size_t ws_bytes, float* grad, float* loss, void* stream);
+lt_status lt_mlp_adam(float* params, float* m, float* v, const float* grad, uint32_t step, float lr,
+                      void* stream);
+lt_status lt_mlp_train_step(float* params, float* m, float* v, float* grad, uint32_t step, float lr,
+                            const float* features, const float* sphericity, const float* target,
+                            const uint32_t* batch_idx, uint32_t batch, void* ws, size_t ws_bytes,
+                            float* loss, void* stream);
+
 /* ------------------------------------------- shape measures, no allocation --
  * Same computation and outputs as lt_shape_measures, for callers that cannot
  * allocate device memory: code that receives device buffers from another

@@ -23,6 +23,8 @@ STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_DIMS", 3: "LT_ER
                 4: "LT_ERR_LABEL_RANGE", 5: "LT_ERR_LABEL_OUTSIDE_MASK", 6: "LT_ERR_CUDA",
                 7: "LT_ERR_NO_DEVICE"}
 FIXED_POINT_SHIFT = 20
+MLP_FEATURES = 48
+MLP_PARAMS = 7361
 
 # exported symbol -> (restype, argtypes)
 _vp, _sz, _i32, _i64, _u32 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int64,
@@ -43,6 +45,14 @@ SIGNATURES = {
     "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
     "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
     "lt_shape_measures_static": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp]),
+    "lt_features_workspace_size": (_sz, [_u32]),
+    "lt_object_features": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "lt_mlp_infer": (_i32, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "lt_mlp_train_workspace_size": (_sz, [_u32]),
+    "lt_mlp_gradients": (_i32, [_vp, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp, _vp, _vp]),
+    "lt_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp]),
+    "lt_mlp_train_step": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp, _vp,
+                                 _u32, _vp, _sz, _vp, _vp]),
     "lt_trace_enable": (_i32, [_i32]),
     "lt_trace_summary": (_i32, [_vp, _i32]),
 }
@@ -195,3 +205,86 @@ def lt_trace_summary():
 
 def lt_workspace_status(ws, stream=None):
     _check(lib.lt_workspace_status(_ptr(ws), ws.numel(), _stream(stream)), "device status")
+
+
+# ------------------------------------------------------- learned sphericity
+def _stats_struct(stats):
+    return ObjectStats(*[stats[k].data_ptr() for k in ("volume", "n_shell", "max_lt2", "sum_lt",
+                                                       "sum_shell_lt")])
+
+
+def lt_object_features(labels, lt2, n_labels, stats, sphericity, roundness, features, ws=None,
+                       stream=None):
+    """features: float32 CUDA tensor [n_labels, 48]; stats as for
+    lt_shape_measures (all five arrays)."""
+    nd, nx, ny, nz = _dims(labels)
+    if ws is None:
+        ws = workspace(lib.lt_features_workspace_size(n_labels), labels.device)
+    st = _stats_struct(stats)
+    _check(lib.lt_object_features(_ptr(labels), _ptr(lt2), n_labels, nd, nx, ny, nz, ctypes.byref(st),
+                                  _ptr(sphericity), _ptr(roundness), _ptr(ws), ws.numel(),
+                                  _ptr(features), _stream(stream)), "lt_object_features")
+    return ws
+
+
+def lt_mlp_infer(params, features, sphericity, s_learned, stream=None):
+    _check(lib.lt_mlp_infer(_ptr(params), _ptr(features), _ptr(sphericity), sphericity.numel(),
+                            _ptr(s_learned), _stream(stream)), "lt_mlp_infer")
+
+
+def lt_mlp_gradients(params, features, sphericity, target, batch_idx, grad, loss=None, ws=None,
+                     stream=None):
+    b = batch_idx.numel()
+    if ws is None:
+        ws = workspace(lib.lt_mlp_train_workspace_size(b), params.device)
+    _check(lib.lt_mlp_gradients(_ptr(params), _ptr(features), _ptr(sphericity), _ptr(target),
+                                _ptr(batch_idx), b, _ptr(ws), ws.numel(), _ptr(grad), _ptr(loss),
+                                _stream(stream)), "lt_mlp_gradients")
+    return ws
+
+
+def lt_mlp_adam(params, m, v, grad, step, lr, stream=None):
+    _check(lib.lt_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
+                           _stream(stream)), "lt_mlp_adam")
+
+
+def lt_mlp_train_step(params, m, v, grad, step, lr, features, sphericity, target, batch_idx,
+                      loss=None, ws=None, stream=None):
+    b = batch_idx.numel()
+    if ws is None:
+        ws = workspace(lib.lt_mlp_train_workspace_size(b), params.device)
+    _check(lib.lt_mlp_train_step(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
+                                 _ptr(features), _ptr(sphericity), _ptr(target), _ptr(batch_idx), b,
+                                 _ptr(ws), ws.numel(), _ptr(loss), _stream(stream)),
+           "lt_mlp_train_step")
+    return ws
+
+
+def train_mlp(params, features, sphericity, target, train_idx, epochs, batch, lr, order_seed=0):
+    """Adam training on the GPU with lt_mlp_train_step. params (FP32 CUDA
+    tensor of MLP_PARAMS) is updated in place; train_idx lists the objects
+    to train on; batches follow a seeded shuffle per epoch. Returns the
+    per-epoch mean loss (host floats)."""
+    import numpy as np
+    import torch
+    dev = params.device
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.empty_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ws = workspace(lib.lt_mlp_train_workspace_size(batch), dev)
+    rng = np.random.default_rng(order_seed)
+    idx = np.asarray(train_idx, dtype=np.int64)
+    step, history = 0, []
+    for _ in range(epochs):
+        perm = idx[rng.permutation(idx.size)]
+        losses = []
+        for s0 in range(0, perm.size - batch + 1, batch):
+            b = torch.from_numpy(perm[s0:s0 + batch].astype(np.int32)).to(dev)
+            step += 1
+            lt_mlp_train_step(params, m, v, grad, step, lr, features, sphericity, target, b, loss,
+                              ws=ws)
+            losses.append(loss.clone())
+        history.append(float(torch.stack(losses).mean().item()) if losses else float("nan"))
+    return history
+

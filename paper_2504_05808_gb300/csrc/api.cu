@@ -376,3 +376,75 @@ int lt_trace_summary(lt_trace_entry* out, int max_entries) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------- learned part
+extern "C" {
+
+size_t lt_features_workspace_size(uint32_t n_labels) { return features_workspace_bytes(n_labels); }
+
+lt_status lt_object_features(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, int ndim,
+                             int64_t nx, int64_t ny, int64_t nz, const lt_object_stats* stats,
+                             const float* sphericity, const float* roundness, void* ws, size_t ws_bytes,
+                             float* features, void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if (n_labels == 0 || !stats) return LT_ERR_INVALID_ARG;
+  const void* ptrs[9] = {labels, lt2, stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt,
+                         sphericity, roundness, features};
+  for (const void* p : ptrs)
+    if ((st = dev_ptr(p)) != LT_OK) return st;
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < features_workspace_bytes(n_labels)) return LT_ERR_WORKSPACE;
+  if ((st = use_device_of(ws)) != LT_OK) return st;
+  return cuda_status(features_launch(labels, lt2, n_labels, d, *stats, sphericity, roundness, ws, features,
+                                     as_stream(stream)));
+}
+
+lt_status lt_mlp_infer(const float* params, const float* features, const float* sphericity, uint32_t n,
+                       float* s_learned, void* stream) {
+  lt_status st;
+  if (n == 0) return LT_OK;
+  const void* ptrs[4] = {params, features, sphericity, s_learned};
+  for (const void* p : ptrs)
+    if ((st = dev_ptr(p)) != LT_OK) return st;
+  return cuda_status(mlp_infer_launch(params, features, sphericity, n, s_learned, as_stream(stream)));
+}
+
+size_t lt_mlp_train_workspace_size(uint32_t batch) { return mlp_train_workspace_bytes(batch); }
+
+lt_status lt_mlp_gradients(const float* params, const float* features, const float* sphericity,
+                           const float* target, const uint32_t* batch_idx, uint32_t batch, void* ws,
+                           size_t ws_bytes, float* grad, float* loss, void* stream) {
+  lt_status st;
+  if (batch == 0) return LT_ERR_INVALID_ARG;
+  const void* ptrs[6] = {params, features, sphericity, target, batch_idx, grad};
+  for (const void* p : ptrs)
+    if ((st = dev_ptr(p)) != LT_OK) return st;
+  if (loss && (st = dev_ptr(loss)) != LT_OK) return st;
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < mlp_train_workspace_bytes(batch)) return LT_ERR_WORKSPACE;
+  if ((st = use_device_of(ws)) != LT_OK) return st;
+  return cuda_status(mlp_grad_launch(params, features, sphericity, target, batch_idx, batch, ws, grad, loss,
+                                     as_stream(stream)));
+}
+
+lt_status lt_mlp_adam(float* params, float* m, float* v, const float* grad, uint32_t step, float lr,
+                      void* stream) {
+  lt_status st;
+  if (step == 0) return LT_ERR_INVALID_ARG;
+  const void* ptrs[4] = {params, m, v, grad};
+  for (const void* p : ptrs)
+    if ((st = dev_ptr(p)) != LT_OK) return st;
+  return cuda_status(mlp_adam_launch(params, m, v, grad, step, lr, as_stream(stream)));
+}
+
+lt_status lt_mlp_train_step(float* params, float* m, float* v, float* grad, uint32_t step, float lr,
+                            const float* features, const float* sphericity, const float* target,
+                            const uint32_t* batch_idx, uint32_t batch, void* ws, size_t ws_bytes,
+                            float* loss, void* stream) {
+  lt_status st = lt_mlp_gradients(params, features, sphericity, target, batch_idx, batch, ws, ws_bytes,
+                                  grad, loss, stream);
+  if (st != LT_OK) return st;
+  return lt_mlp_adam(params, m, v, grad, step, lr, stream);
+}
+
+}  // extern "C"

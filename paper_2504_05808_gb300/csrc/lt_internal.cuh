@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstddef>
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -65,6 +66,20 @@ size_t shape_workspace_bytes(uint32_t n_labels);
 cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
                          const lt_object_stats* stats, cudaStream_t s);
+
+// learned.cu
+size_t features_workspace_bytes(uint32_t n_labels);
+cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                            const lt_object_stats& st, const float* S, const float* R, void* body, float* F,
+                            cudaStream_t s);
+cudaError_t mlp_infer_launch(const float* params, const float* F, const float* S, uint32_t n, float* out,
+                             cudaStream_t s);
+size_t mlp_train_workspace_bytes(uint32_t batch);
+cudaError_t mlp_grad_launch(const float* params, const float* F, const float* S, const float* target,
+                            const uint32_t* idx, uint32_t batch, void* ws, float* grad, float* loss,
+                            cudaStream_t s);
+cudaError_t mlp_adam_launch(float* params, float* m, float* v, const float* grad, uint32_t step, float lr,
+                            cudaStream_t s);
 
 // Brackets one kernel launch with trace events when tracing is enabled
 // (see lt_trace_enable). Construct right before the launch; the destructor

@@ -120,3 +120,32 @@ def workload(name: str, seed: int = 0):
     else:
         raise KeyError(name)
     return m, l, c + 1
+
+
+def mlp_initial_params(seed: int, n_features: int = 48, hidden: int = 64):
+    """Seeded initial parameters of the 48-64-64-1 sphericity-correction
+    network (random inputs shared by the CUDA path and the oracle): weights
+    uniform in +-sqrt(6 / fan_in) (the last layer scaled by 0.1), biases 0.
+    Layout: W1[48][64], b1[64], W2[64][64], b2[64], w3[64], b3 (float32)."""
+    import math
+    rng = np.random.default_rng(seed)
+    n = n_features * hidden + hidden + hidden * hidden + hidden + hidden + 1
+    p = np.zeros(n, np.float32)
+    o_b1 = n_features * hidden
+    o_w2 = o_b1 + hidden
+    o_b2 = o_w2 + hidden * hidden
+    o_w3 = o_b2 + hidden
+    p[:o_b1] = rng.uniform(-1, 1, o_b1) * math.sqrt(6.0 / n_features)
+    p[o_w2:o_b2] = rng.uniform(-1, 1, hidden * hidden) * math.sqrt(6.0 / hidden)
+    p[o_w3:o_w3 + hidden] = rng.uniform(-1, 1, hidden) * math.sqrt(6.0 / hidden) * 0.1
+    return p
+
+
+def training_particles(edge: int, seed: int):
+    """Particles of the 512^3 mix with equivalent radii widened to 3-18
+    voxels (so that the smaller particles of the 1024^3 volume are covered)
+    at the same packing: (mask, labels, n_labels)."""
+    n = particles_per_volume(edge, voxels_per_particle=512**3 / 5000 / 2.0)
+    m, l, c = packed((edge, edge, edge), n, 3.0, 18.0, seed)
+    return m, l, c + 1
+
