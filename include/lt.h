@@ -145,6 +145,48 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
                             float* sphericity, float* roundness, const lt_object_stats* stats,
                             void* stream);
 
+/* ---------------------------------------------------------- batched form --
+ * Many volumes (2D and 3D, uneven sizes) measured as one unit of work. The
+ * batch owns no device memory: `ws` (lt_batch_workspace_size bytes) holds
+ * every volume's workspace. lt_batch_create checks the volumes, copies the
+ * lookup tables to the device if needed and records the whole batch (for
+ * each volume the kernels of lt_measure) into a CUDA graph whose volumes sit
+ * on `branches` parallel branches (largest volumes first, each to the least
+ * loaded branch), so small volumes run side by side. lt_batch_run launches
+ * that graph on `stream` (one launch per batch); lt_batch_run_eager issues
+ * the same kernels volume after volume on `stream`, the per-volume baseline.
+ * lt_batch_status waits for `stream` and returns the first device-detected
+ * error of any volume. lt_batch_autotune times candidate settings (branch
+ * count, EDT column-tile width, ridge z-chunk, paint grid) on the batch
+ * itself, one setting at a time from the defaults, keeps the fastest and
+ * rebuilds the graph; results are cached in the JSON file `cache_path`
+ * (NULL: no cache) under the GPU name and the batch's shape class, and a
+ * cached entry is reused without timing. The batch and its graph are host
+ * objects: lt_batch_destroy releases them. Host-side calls (create,
+ * autotune, destroy) are not thread-safe for the same batch. */
+typedef struct lt_volume {
+  int32_t ndim;
+  uint32_t n_labels;
+  int64_t nx, ny, nz;
+  const uint8_t* mask;
+  const uint32_t* labels;
+  uint32_t* dt2;
+  uint32_t* lt2;
+  float* sphericity;
+  float* roundness;
+} lt_volume;
+typedef struct lt_batch lt_batch;
+size_t lt_batch_workspace_size(const lt_volume* vols, int n_vols);
+lt_status lt_batch_create(const lt_volume* vols, int n_vols, void* ws, size_t ws_bytes, int branches,
+                          lt_batch** batch);
+lt_status lt_batch_run(lt_batch* batch, void* stream);
+lt_status lt_batch_run_eager(lt_batch* batch, void* stream);
+lt_status lt_batch_status(lt_batch* batch, void* stream);
+lt_status lt_batch_autotune(lt_batch* batch, void* stream, const char* cache_path);
+/* current settings: branches, EDT tile width, ridge z-chunk, paint CTAs per SM */
+lt_status lt_batch_settings(const lt_batch* batch, int32_t out[4]);
+void lt_batch_destroy(lt_batch* batch);
+
 /* ------------------------------------------------ learned sphericity --
  * A correction of S_LT toward the strict (mesh) sphericity of Eq. 1 by a
  * small network; the paper has none, so its definition is this library's:

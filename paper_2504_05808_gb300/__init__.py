@@ -53,6 +53,14 @@ SIGNATURES = {
     "lt_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp]),
     "lt_mlp_train_step": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp, _vp,
                                  _u32, _vp, _sz, _vp, _vp]),
+    "lt_batch_workspace_size": (_sz, [_vp, _i32]),
+    "lt_batch_create": (_i32, [_vp, _i32, _vp, _sz, _i32, _vp]),
+    "lt_batch_run": (_i32, [_vp, _vp]),
+    "lt_batch_run_eager": (_i32, [_vp, _vp]),
+    "lt_batch_status": (_i32, [_vp, _vp]),
+    "lt_batch_autotune": (_i32, [_vp, _vp, ctypes.c_char_p]),
+    "lt_batch_settings": (_i32, [_vp, _vp]),
+    "lt_batch_destroy": (None, [_vp]),
     "lt_trace_enable": (_i32, [_i32]),
     "lt_trace_summary": (_i32, [_vp, _i32]),
 }
@@ -287,4 +295,66 @@ def train_mlp(params, features, sphericity, target, train_idx, epochs, batch, lr
             losses.append(loss.clone())
         history.append(float(torch.stack(losses).mean().item()) if losses else float("nan"))
     return history
+
+
+# ------------------------------------------------------------- batched form
+class Volume(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n_labels", ctypes.c_uint32), ("nx", _i64), ("ny", _i64),
+                ("nz", _i64), ("mask", _vp), ("labels", _vp), ("dt2", _vp), ("lt2", _vp),
+                ("sphericity", _vp), ("roundness", _vp)]
+
+
+class Batch:
+    """Many volumes measured by one CUDA graph launch (lt_batch_*).
+
+    items: list of dicts with CUDA tensors mask, labels, dt2, lt2,
+    sphericity, roundness and the int n_labels. The tensors must stay alive
+    and in place while the batch exists (the graph holds their addresses).
+    """
+
+    def __init__(self, items, branches=4, device=None):
+        import torch
+        self.items = items
+        arr = (Volume * len(items))()
+        for a, it in zip(arr, items):
+            nd, nx, ny, nz = _dims(it["mask"])
+            a.ndim, a.n_labels, a.nx, a.ny, a.nz = nd, int(it["n_labels"]), nx, ny, nz
+            for k in ("mask", "labels", "dt2", "lt2", "sphericity", "roundness"):
+                setattr(a, k, it[k].data_ptr())
+        self._vols = arr
+        dev = device if device is not None else items[0]["mask"].device
+        self.ws = workspace(lib.lt_batch_workspace_size(arr, len(items)), dev)
+        h = ctypes.c_void_p()
+        _check(lib.lt_batch_create(arr, len(items), _ptr(self.ws), self.ws.numel(), int(branches),
+                                   ctypes.byref(h)), "lt_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib.lt_batch_run(self.handle, _stream(stream)), "lt_batch_run")
+
+    def run_eager(self, stream=None):
+        _check(lib.lt_batch_run_eager(self.handle, _stream(stream)), "lt_batch_run_eager")
+
+    def status(self, stream=None):
+        _check(lib.lt_batch_status(self.handle, _stream(stream)), "lt_batch_status")
+
+    def autotune(self, cache_path=None, stream=None):
+        p = cache_path.encode() if cache_path else None
+        _check(lib.lt_batch_autotune(self.handle, _stream(stream), p), "lt_batch_autotune")
+
+    def settings(self):
+        out = (ctypes.c_int32 * 4)()
+        _check(lib.lt_batch_settings(self.handle, out), "lt_batch_settings")
+        return {"branches": out[0], "edt_tx": out[1], "ridge_z": out[2], "paint_bpsm": out[3]}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.lt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

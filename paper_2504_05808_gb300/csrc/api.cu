@@ -89,16 +89,36 @@ size_t measure_body_bytes(const Dims& d, uint32_t n_labels) {
 
 lt_status run_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
                       void* ws, uint32_t* dt2, uint32_t* lt2, float* S, float* R, cudaStream_t s) {
-  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
-  void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
-  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
-  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(body), s);
-  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s);
-  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
-  return cuda_status(e);
+  return cuda_status(ltk::measure_launch(mask, labels, n_labels, d, ws, dt2, lt2, S, R, s, Tuning()));
 }
 
 }  // namespace
+
+namespace ltk {
+
+lt_status make_dims_checked(int ndim, int64_t nx, int64_t ny, int64_t nz, Dims* d) {
+  return make_dims(ndim, nx, ny, nz, d);
+}
+
+size_t measure_ws_bytes(const Dims& d, uint32_t n_labels) {
+  return sizeof(WsHeader) + measure_body_bytes(d, n_labels);
+}
+
+cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
+                           void* ws, uint32_t* dt2, uint32_t* lt2, float* S, float* R, cudaStream_t s,
+                           const Tuning& tu) {
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(body), s, tu);
+  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s, tu);
+  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
+  return e;
+}
+
+lt_status device_ptr_ok(const void* p) { return dev_ptr(p); }
+
+}  // namespace ltk
 
 extern "C" {
 
@@ -304,6 +324,11 @@ TraceScope::TraceScope(const char* name, cudaStream_t s) : slot_(-1), s_(s) {
   TraceState& t = trace();
   std::lock_guard<std::mutex> g(t.mu);
   if (!t.enabled) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // no event timing inside graph capture
+  }
   std::pair<cudaEvent_t, cudaEvent_t> ev;
   if (!t.pool.empty()) {
     ev = t.pool.back();

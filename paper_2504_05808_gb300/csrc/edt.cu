@@ -221,8 +221,9 @@ cudaError_t launch_cols(const char* name, uint32_t* data, int L, size_t sp, int 
 }
 
 cudaError_t col_pass(const char* name, uint32_t* data, int L, size_t sp, int nx, size_t so, int nother,
-                     uint32_t* tmp, size_t n, cudaStream_t s) {
+                     uint32_t* tmp, size_t n, cudaStream_t s, int tx_small) {
   const bool vec = (nx % 4) == 0;
+  if (L <= 512 && tx_small == 16) return launch_cols<16>(name, data, L, sp, nx, so, nother, vec, s);
   if (L <= 512) return launch_cols<32>(name, data, L, sp, nx, so, nother, vec, s);
   if (L <= 1024) return launch_cols<16>(name, data, L, sp, nx, so, nother, vec, s);
   if (L <= 2048) return launch_cols<8>(name, data, L, sp, nx, so, nother, vec, s);
@@ -239,13 +240,20 @@ cudaError_t col_pass(const char* name, uint32_t* data, int L, size_t sp, int nx,
 
 }  // namespace
 
+cudaError_t edt_prepare_device() {
+  cudaError_t e = allow_smem((const void*)edt_cols_kernel<32>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<16>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<8>, 64 * 1024);
+  return e;
+}
+
 size_t edt_workspace_bytes(const Dims& d) {
   const int longest = d.ndim == 3 ? (d.ny > d.nz ? d.ny : d.nz) : d.ny;
   return longest > 2048 ? (size_t)d.n * sizeof(uint32_t) : 0;
 }
 
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
-                       cudaStream_t s) {
+                       cudaStream_t s, const Tuning& tu) {
   const uint32_t nrows = (uint32_t)d.ny * (uint32_t)d.nz;
   const unsigned blocks = (nrows + 7) / 8;
   {
@@ -259,10 +267,10 @@ cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32
   if (e != cudaSuccess) return e;
   const size_t plane = (size_t)d.nx * d.ny;
   // y: columns of length ny, stride nx; one tile row per z.
-  e = col_pass("edt_cols_y", dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s);
+  e = col_pass("edt_cols_y", dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s, tu.edt_tx_small);
   if (e != cudaSuccess || d.ndim == 2) return e;
   // z: columns of length nz, stride nx*ny; one tile row per y.
-  return col_pass("edt_cols_z", dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s);
+  return col_pass("edt_cols_z", dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s, tu.edt_tx_small);
 }
 
 }  // namespace ltk

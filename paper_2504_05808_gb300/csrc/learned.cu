@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const float* __restrict_
   }
 }
 
-// Per-sample forward and backward vectors of a batch. Scratch per sample:
-// x[48], h1[64], h2[64], g1[64] (d loss / d pre1), g2[64] (d loss / d pre2),
-// g_out.
+// Per-sample forward and backward vectors of a batch. Scratch per sample
+// (kSampleStride floats): x[48], h1[64], h2[64], g1[64] (d loss / d pre1),
+// g2[64] (d loss / d pre2), g_out, 3 unused.
 constexpr int kSampleStride = kF + 4 * kH + 4;
 
 __global__ void __launch_bounds__(128) mlp_backprop_kernel(const float* __restrict__ params,
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) mlp_backprop_kernel(const float* __restri
   const float r = S[o] + out - target[o];
   const float g_out = 2.0f * r / (float)batch;
   sq[b] = r * r;
-  g2[kH + kH] = g_out;  // stored after g2 (slot kSampleStride - 4)
+  g2[kH] = g_out;  // the slot after g2 (offset kF + 4 kH of the sample)
 #pragma unroll 4
   for (int j = 0; j < kH; ++j) g2[j] = pre2[j] > 0.0f ? g_out * net.w3[j] : 0.0f;
 #pragma unroll 4
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const float* __restrict__
     const float* h2 = h1 + kH;
     const float* g1 = h2 + kH;
     const float* g2 = g1 + kH;
-    const float g_out = g2[2 * kH];
+    const float g_out = g2[kH];
     float t;
     if (p < kOffB1) t = x[p / kH] * g1[p % kH];
     else if (p < kOffW2) t = g1[p - kOffB1];

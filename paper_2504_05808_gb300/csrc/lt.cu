@@ -173,7 +173,7 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // applies the containment test and appends kept centres.
 //
 // A CTA owns a 32 x 8 (x, y) column tile and marches along z through
-// kRidgeZ planes, keeping three halo planes (34 x 10) of (DT2, label) pairs
+// RZ planes, keeping three halo planes (34 x 10) of (DT2, label) pairs
 // in shared memory; outside the array the halo holds (0, 0), which never
 // matches an object label. Per plane, the labelled foreground voxels are
 // compacted to the front of the CTA so that the 26-neighbour (8 in 2D) test
@@ -187,9 +187,9 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // more higher-ranked same-label neighbours (5 bits each, 31 for none).
 constexpr int kTX = 32, kTY = 8;
 constexpr int kHX = kTX + 2, kHY = kTY + 2, kPlane = kHX * kHY;
-constexpr int kRidgeZ = 16, kRidgeFlush = 2;
+constexpr int kRidgeFlush = 2;
 
-template <int NDIM>
+template <int NDIM, int RZ>
 __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
   __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s;
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int z0 = NDIM == 3 ? blockIdx.z * kRidgeZ : 0;
-  const int z1 = NDIM == 3 ? min(d.nz, z0 + kRidgeZ) : 1;
+  const int z0 = NDIM == 3 ? blockIdx.z * RZ : 0;
+  const int z1 = NDIM == 3 ? min(d.nz, z0 + RZ) : 1;
   const size_t plane = (size_t)d.nx * d.ny;
   const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
   const unsigned below = (1u << lane) - 1u;
@@ -653,23 +653,30 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
 
 size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint4)); }
 
+cudaError_t lt_prepare_device() { return ensure_tables(); }
+
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
-                      WsHeader* hdr, void* body, cudaStream_t s) {
+                      WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
   uint4* surv = reinterpret_cast<uint4*>(body);
-  dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY,
-            d.ndim == 3 ? (d.nz + kRidgeZ - 1) / kRidgeZ : 1);
+  const int rz = tu.ridge_z == 8 || tu.ridge_z == 32 ? tu.ridge_z : 16;
+  dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY, d.ndim == 3 ? (d.nz + rz - 1) / rz : 1);
   {
     TraceScope t("lt_ridge", s);
-    if (d.ndim == 3)
-      lt_ridge_kernel<3><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+    if (d.ndim == 2)
+      lt_ridge_kernel<2, 16><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+    else if (rz == 8)
+      lt_ridge_kernel<3, 8><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+    else if (rz == 32)
+      lt_ridge_kernel<3, 32><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
     else
-      lt_ridge_kernel<2><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+      lt_ridge_kernel<3, 16><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const unsigned pblocks = (unsigned)sm_count() * 8;
+  const int bps = tu.paint_blocks_per_sm > 0 ? tu.paint_blocks_per_sm : 8;
+  const unsigned pblocks = (unsigned)(sm_count() * bps);
   {
     TraceScope t("lt_paint", s);
     if (d.ndim == 3)

@@ -52,15 +52,25 @@ struct ShapeAcc {
   unsigned long long* sum_shell_lt;
 };
 
+// Launch parameters the batch autotuner may change (defaults: single calls).
+struct Tuning {
+  int edt_tx_small = 32;        // EDT column-tile width for axes <= 512 (32 or 16)
+  int ridge_z = 16;             // z planes per ridge CTA (8, 16 or 32)
+  int paint_blocks_per_sm = 8;  // persistent paint grid, CTAs per SM
+};
+
 // ---- host launchers (each returns cudaSuccess or the launch error) ----
 // edt.cu
 size_t edt_workspace_bytes(const Dims& d);
+cudaError_t edt_prepare_device();  // kernel attributes; call before capture
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
-                       cudaStream_t s);
+                       cudaStream_t s, const Tuning& tu = Tuning());
 // lt.cu
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
-                      WsHeader* hdr, void* body, cudaStream_t s);
+                      WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu = Tuning());
+// copies the lookup tables to the current device (first use); call before capture
+cudaError_t lt_prepare_device();
 // shape.cu
 size_t shape_workspace_bytes(uint32_t n_labels);
 cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
@@ -93,6 +103,14 @@ class TraceScope {
   int slot_;
   cudaStream_t s_;
 };
+
+// api.cu: checked dimensions, workspace of one lt_measure, and its launch
+lt_status make_dims_checked(int ndim, int64_t nx, int64_t ny, int64_t nz, Dims* d);
+size_t measure_ws_bytes(const Dims& d, uint32_t n_labels);
+cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
+                           void* ws, uint32_t* dt2, uint32_t* lt2, float* S, float* R, cudaStream_t s,
+                           const Tuning& tu);
+lt_status device_ptr_ok(const void* p);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

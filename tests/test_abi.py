@@ -90,3 +90,23 @@ def test_product_path_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lt_oracle" not in text, f
+
+
+def test_batch_argument_errors_need_no_gpu(lt):
+    L = lt.lib
+    E = {v: k for k, v in lt.STATUS_NAMES.items()}
+    assert L.lt_batch_workspace_size(None, 0) == 0
+    h = ctypes.c_void_p()
+    assert L.lt_batch_create(None, 0, None, 0, 1, ctypes.byref(h)) == E["LT_ERR_INVALID_ARG"]
+    vols = (lt.Volume * 2)()
+    vols[0].ndim, vols[0].n_labels, vols[0].nx, vols[0].ny, vols[0].nz = 3, 5, 64, 64, 64
+    vols[1].ndim, vols[1].n_labels, vols[1].nx, vols[1].ny, vols[1].nz = 2, 3, 100, 50, 1
+    one = L.lt_measure_workspace_size(5, 3, 64, 64, 64)
+    two = L.lt_measure_workspace_size(3, 2, 100, 50, 1)
+    assert L.lt_batch_workspace_size(vols, 2) >= one + two
+    vols[1].nz = 2  # 2D with nz != 1
+    assert L.lt_batch_workspace_size(vols, 2) == 0
+    # null device pointers are rejected before anything is recorded
+    vols[1].nz = 1
+    assert L.lt_batch_create(vols, 2, None, 0, 2, ctypes.byref(h)) == E["LT_ERR_INVALID_ARG"]
+    assert L.lt_batch_run(None, None) == E["LT_ERR_INVALID_ARG"]
