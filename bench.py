@@ -38,6 +38,11 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-sphericity evaluation")
+    p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--learned-1024", action="store_true",
+                   help="also evaluate the learned correction on the 1024^3 volume (slow)")
     return p.parse_args()
 
 
@@ -107,7 +112,7 @@ def algorithmic_bytes(name, n, n_surv):
         "edt_rows_x": 5 * n,          # mask in, g^2 out
         "edt_cols_y": 8 * n,          # u32 in, u32 out
         "edt_cols_z": 8 * n,
-        "lt_ridge": 12 * n + 8 * n_surv,  # DT2, labels in; LT2 cleared; centres out
+        "lt_ridge": 12 * n + 16 * n_surv,  # DT2, labels in; LT2 cleared; centre records out
         "shape_reduce": 8 * n,        # labels, LT2 in
     }
     return table.get(name)
@@ -130,6 +135,151 @@ def cpu_oracle_rate(mask, labels, n_labels, target_s=15.0):
             break
         t = min(nz, max(t * 2, int(t * target_s / max(dt, 1e-3) / 2)))
     return m.size / dt / 1e6, f"z-slab {m.shape[0]}x{m.shape[1]}x{m.shape[2]} of the workload", dt
+
+
+def measure_batch(lt, args, dev):
+    """Batched form: 64 uneven 3D volumes + 8 2D 4096^2 masks as one graph
+    launch (autotuned), against the same kernels issued volume by volume."""
+    import tempfile
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    vols = synth.batch_workload(args.seed)
+    gen_s = time.perf_counter() - t0
+    items = []
+    for m, l, n in vols:
+        items.append({"mask": torch.from_numpy(m).to(dev),
+                      "labels": torch.from_numpy(l.view(np.int32)).to(dev),
+                      "dt2": torch.empty(m.shape, dtype=torch.int32, device=dev),
+                      "lt2": torch.empty(m.shape, dtype=torch.int32, device=dev),
+                      "sphericity": torch.empty(n, dtype=torch.float32, device=dev),
+                      "roundness": torch.empty(n, dtype=torch.float32, device=dev), "n_labels": n})
+    nvox = sum(m.size for m, _, _ in vols)
+    del vols
+    batch = lt.Batch(items, branches=4)
+    cache = os.environ.get("LT_AUTOTUNE_CACHE") or os.path.join(tempfile.mkdtemp(), "autotune.json")
+    batch.autotune(cache)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_graph = timed(batch.run, args.batch_steps)
+    ms_eager = timed(batch.run_eager, max(3, args.batch_steps // 2))
+    batch.status()
+    out = {"value": nvox / (ms_graph * 1e-3) / 1e6, "unit": UNIT, "ms_per_batch": ms_graph,
+           "eager_value": nvox / (ms_eager * 1e-3) / 1e6, "eager_ms_per_batch": ms_eager,
+           "volumes": len(items), "voxels": nvox, "settings": batch.settings(),
+           "workload": "64 cubic volumes, edge U{64..384}, 512^3 mix; 8 x 2D 4096^2 ellipses",
+           "generate_s": gen_s}
+    batch.close()
+    return out
+
+
+def learned_eval(lt, args, dev):
+    """Train the correction on particles of 5 volumes on the GPU, report MAE
+    against strict sphericity on a 6th (held out), and per-object costs."""
+    import torch
+    import synth
+    import oracle.learned as L
+    feats, S_all, T_all, t_feat, n_obj_feat = [], [], [], 0.0, 0
+    for seed in range(6):
+        m, lab, n = synth.training_particles(160, 100 + seed)
+        mt = torch.from_numpy(m).to(dev)
+        labt = torch.from_numpy(lab.view(np.int32)).to(dev)
+        dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
+        lt2 = torch.empty_like(dt2)
+        S = torch.empty(n, dtype=torch.float32, device=dev)
+        R = torch.empty_like(S)
+        stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
+        stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
+        lt.lt_edt(mt, dt2)
+        lt.lt_local_thickness(dt2, labt, lt2)
+        lt.lt_shape_measures(labt, lt2, n, S, R, stats)
+        F = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
+        fws = lt.lt_object_features(labt, lt2, n, stats, S, R, F)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lt.lt_object_features(labt, lt2, n, stats, S, R, F, ws=fws)
+        e1.record()
+        torch.cuda.synchronize()
+        t_feat += e0.elapsed_time(e1)
+        n_obj_feat += n - 1
+        T = L.strict_sphericity(lab, n)
+        Sn = S.cpu().numpy()
+        ok = np.isfinite(T) & np.isfinite(Sn)
+        ok[0] = False
+        feats.append(F.cpu().numpy()[ok])
+        S_all.append(Sn[ok])
+        T_all.append(T[ok].astype(np.float32))
+    ntr = sum(len(x) for x in S_all[:5])
+    F = torch.from_numpy(np.concatenate(feats)).to(dev)
+    S = torch.from_numpy(np.concatenate(S_all)).to(dev)
+    T = torch.from_numpy(np.concatenate(T_all)).to(dev)
+    p = torch.from_numpy(synth.mlp_initial_params(0)).to(dev)
+    t0 = time.perf_counter()
+    hist = lt.train_mlp(p, F, S, T, np.arange(ntr), epochs=150, batch=256, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    out = torch.empty(len(S) - ntr, dtype=torch.float32, device=dev)
+    Fh, Sh = F[ntr:].contiguous(), S[ntr:].contiguous()
+    lt.lt_mlp_infer(p, Fh, Sh, out)
+    torch.cuda.synchronize()
+    held_T = T_all[5].astype(np.float64)
+    res = {"mae_plain": float(np.abs(S_all[5] - held_T).mean()),
+           "mae_learned": float(np.abs(out.cpu().numpy() - held_T).mean()),
+           "objects_train": int(ntr), "objects_held_out": int(len(held_T)),
+           "train_s": train_s, "final_train_loss": hist[-1],
+           "target": "strict sphericity: smoothed marching-tetrahedra mesh (FP64 oracle)",
+           "features_ns_per_object": t_feat * 1e6 / max(1, n_obj_feat)}
+    # inference cost per object at scale (1M objects of random features)
+    big = 1 << 20
+    Fb = torch.rand((big, lt.MLP_FEATURES), device=dev)
+    Sb = torch.rand(big, device=dev)
+    ob = torch.empty(big, device=dev)
+    lt.lt_mlp_infer(p, Fb, Sb, ob)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        lt.lt_mlp_infer(p, Fb, Sb, ob)
+    e1.record()
+    torch.cuda.synchronize()
+    res["infer_ns_per_object"] = e0.elapsed_time(e1) / 5 * 1e6 / big
+    if args.learned_1024:
+        m, lab, n = synth.workload("particles_3d_1024", 0)
+        mt = torch.from_numpy(m).to(dev)
+        labt = torch.from_numpy(lab.view(np.int32)).to(dev)
+        dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
+        lt2 = torch.empty_like(dt2)
+        Sg = torch.empty(n, dtype=torch.float32, device=dev)
+        Rg = torch.empty_like(Sg)
+        stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
+        stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
+        lt.lt_edt(mt, dt2)
+        lt.lt_local_thickness(dt2, labt, lt2)
+        lt.lt_shape_measures(labt, lt2, n, Sg, Rg, stats)
+        Fg = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
+        lt.lt_object_features(labt, lt2, n, stats, Sg, Rg, Fg)
+        og = torch.empty(n, dtype=torch.float32, device=dev)
+        lt.lt_mlp_infer(p, Fg, Sg, og)
+        T = L.strict_sphericity(lab, n)
+        Sn, On = Sg.cpu().numpy(), og.cpu().numpy()
+        ok = np.isfinite(T) & np.isfinite(Sn)
+        ok[0] = False
+        res["volume_1024"] = {"objects": int(ok.sum()),
+                              "mae_plain": float(np.abs(Sn[ok] - T[ok]).mean()),
+                              "mae_learned": float(np.abs(On[ok] - T[ok]).mean())}
+    return res
 
 
 def run_reference(args):
@@ -271,6 +421,15 @@ def main():
         roof["algorithmic_bytes"] = ab
     gpu_launches = sum(v[0] for v in trace.values())
 
+    batched = None
+    if not args.no_batch:
+        del wsh
+        torch.cuda.empty_cache()
+        batched = measure_batch(lt, args, dev)
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = learned_eval(lt, args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, _ = cpu_oracle_rate(mask, labels, n_labels)
@@ -287,7 +446,7 @@ def main():
                           "seed": args.seed, "parallelism": f"replicas{world}",
                           "l2": "inputs larger than L2 (no flush needed)"},
                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": gpu_launches, "clocks": clk}
+               "gpu_launches": gpu_launches, "clocks": clk, "batched": batched, "learned": learned}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -53,10 +53,11 @@ struct ShapeAcc {
 };
 
 // Launch parameters the batch autotuner may change (defaults: single calls).
+// Defaults: the autotuner's choice for the 512^3 particle volume on GB300.
 struct Tuning {
-  int edt_tx_small = 32;        // EDT column-tile width for axes <= 512 (32 or 16)
-  int ridge_z = 16;             // z planes per ridge CTA (8, 16 or 32)
-  int paint_blocks_per_sm = 8;  // persistent paint grid, CTAs per SM
+  int edt_tx_small = 16;        // EDT column-tile width for axes <= 512 (32 or 16)
+  int ridge_z = 32;             // z planes per ridge CTA (8, 16 or 32)
+  int paint_blocks_per_sm = 6;  // persistent paint grid, CTAs per SM
 };
 
 // ---- host launchers (each returns cudaSuccess or the launch error) ----

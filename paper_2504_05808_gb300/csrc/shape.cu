@@ -89,6 +89,105 @@ __global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __res
   }
 }
 
+// Vector form for nx % 4 == 0: a thread covers 4 consecutive voxels of a
+// row (16-byte loads of labels, LT2 and the neighbouring rows), adds the
+// voxels of its first nonzero label locally (voxels of another nonzero label
+// in the same 4, which needs touching objects, go straight to the atomics),
+// then runs of equal labels across the warp are combined as above.
+__device__ __forceinline__ uint32_t comp(const uint4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
+                                                            const uint32_t* __restrict__ lt2, Dims d,
+                                                            uint32_t n_labels, ShapeAcc acc,
+                                                            WsHeader* __restrict__ hdr) {
+  const int lane = threadIdx.x & 31;
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const bool in = x0 < d.nx && y < d.ny;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x0 : 0;
+  uint4 L = make_uint4(0u, 0u, 0u, 0u);
+  if (in) L = *reinterpret_cast<const uint4*>(labels + v);
+  const bool any = (L.x | L.y | L.z | L.w) != 0u;
+  if (__ballot_sync(kFull, any) == 0) return;  // uniform per warp
+  uint32_t lab = 0, pk = 0, mx = 0;
+  unsigned long long q = 0, qs = 0;
+  bool bad = false;
+  if (any) {
+    const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
+    const uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
+    uint4 Zm = zero, Zp = zero;
+    if (NDIM == 3) {
+      if (z > 0) Zm = *reinterpret_cast<const uint4*>(labels + v - sz);
+      if (z + 1 < d.nz) Zp = *reinterpret_cast<const uint4*>(labels + v + sz);
+    }
+    const uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
+    const uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t l = comp(L, k);
+      if (l == 0) continue;
+      if (l >= n_labels) {
+        bad = true;
+        continue;
+      }
+      const uint32_t left = k == 0 ? xl : comp(L, k - 1), right = k == 3 ? xr : comp(L, k + 1);
+      bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l;
+      if (NDIM == 3) s = s || comp(Zm, k) != l || comp(Zp, k) != l;
+      const uint32_t t = comp(T, k);
+      const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
+      if (lab == 0) lab = l;
+      if (l == lab) {
+        pk += 1u | (s ? 1u << 16 : 0u);
+        mx = max(mx, t);
+        q += qq;
+        qs += s ? qq : 0ull;
+      } else {  // a second object within the same four voxels
+        atomicAdd(acc.volume + l, 1u);
+        if (s) atomicAdd(acc.n_shell + l, 1u);
+        atomicAdd(acc.sum_lt + l, (unsigned long long)qq);
+        if (s) atomicAdd(acc.sum_shell_lt + l, (unsigned long long)qq);
+        atomicMax(acc.max_lt2 + l, t);
+      }
+    }
+  }
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(&hdr->error, ERR_LABEL_RANGE);
+  // segmented inclusive scan over runs of equal labels
+  const uint32_t lprev = __shfl_up_sync(kFull, lab, 1);
+  int seg = (lane == 0 || lprev != lab) ? lane : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, seg, o);
+    if (lane >= o) seg = max(seg, t);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(kFull, pk, o);
+    const unsigned long long b = __shfl_up_sync(kFull, q, o);
+    const unsigned long long c = __shfl_up_sync(kFull, qs, o);
+    const uint32_t m = __shfl_up_sync(kFull, mx, o);
+    if (lane - o >= seg) {
+      pk += a;
+      q += b;
+      qs += c;
+      mx = max(mx, m);
+    }
+  }
+  const uint32_t lnext = __shfl_down_sync(kFull, lab, 1);
+  if (lab && (lane == 31 || lnext != lab)) {
+    atomicAdd(acc.volume + lab, pk & 0xFFFFu);
+    atomicAdd(acc.n_shell + lab, pk >> 16);
+    atomicAdd(acc.sum_lt + lab, q);
+    atomicAdd(acc.sum_shell_lt + lab, qs);
+    atomicMax(acc.max_lt2 + lab, mx);
+  }
+}
+
 __device__ double spheroid_area(double a, double c) {
   const double pi = 3.141592653589793;
   if (c == a) return 4.0 * pi * a * a;
@@ -159,8 +258,16 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
   acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
   cudaError_t e = cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
   if (e != cudaSuccess) return e;
-  dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
-  {
+  if (d.nx % 4 == 0) {
+    // 64 threads (256 voxels) per row, 4 rows per CTA
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    TraceScope t("shape_reduce", s);
+    if (d.ndim == 3)
+      shape_reduce4_kernel<3><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+    else
+      shape_reduce4_kernel<2><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+  } else {
+    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
     TraceScope t("shape_reduce", s);
     if (d.ndim == 3)
       shape_reduce_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);

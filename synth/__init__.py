@@ -149,3 +149,18 @@ def training_particles(edge: int, seed: int):
     m, l, c = packed((edge, edge, edge), n, 3.0, 18.0, seed)
     return m, l, c + 1
 
+
+
+def batch_workload(seed: int = 0, n3d: int = 64, n2d: int = 8, edge_lo: int = 64, edge_hi: int = 384,
+                   edge2d: int = 4096):
+    """Uneven batch: n3d cubic volumes with edges uniform in [edge_lo, edge_hi]
+    (the 512^3 particle mix at the same density) and n2d dense 2D ellipse
+    masks of edge2d^2. Returns a list of (mask, labels, n_labels)."""
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(edge_lo, edge_hi + 1, n3d)
+    out = []
+    for i, e in enumerate(edges):
+        out.append(workload(f"particles_3d_{int(e)}", seed * 1000 + i))
+    for j in range(n2d):
+        out.append(workload(f"ellipses_2d_{edge2d}", seed * 1000 + 500 + j))
+    return out
