@@ -118,6 +118,24 @@ def algorithmic_bytes(name, n, n_surv):
     return table.get(name)
 
 
+# DRAM bytes (read + write) per launch from an ncu capture of the same kernel
+# source on the same workload; None until captured for the current kernels.
+TRAFFIC = {}
+
+
+def update_rate_probe(lt, dev):
+    """Atomic-max update ceilings (G updates/s): one line per warp instruction
+    or one line per lane, on a 32 MiB (L2-resident) and a 512 MiB buffer."""
+    import torch
+    out = {}
+    for words, tag in ((1 << 23, "l2"), (1 << 27, "hbm")):
+        buf = torch.zeros(words, dtype=torch.int32, device=dev)
+        for pat, pname in ((0, "line_per_warp"), (1, "line_per_lane")):
+            out[f"{pname}_{tag}"] = lt.lt_probe_update_rate(buf, pat, reps=5) / 1e9
+        del buf
+    return out
+
+
 def cpu_oracle_rate(mask, labels, n_labels, target_s=15.0):
     """The oracle as it stands on a z-slab of the workload; slab grown until
     one run takes about target_s seconds (bounded)."""
@@ -354,8 +372,8 @@ def main():
     for _ in range(max(3, args.warmup)):
         lt.lt_measure(m, l, n_labels, dt2, lt2, S, R, ws=ws)
     lt.lt_workspace_status(ws)
-    hdr = ws[:16].view(torch.int32).cpu()
-    n_surv = int(hdr[2].item()) + int(hdr[3].item())
+    counters = lt.lt_workspace_counters(ws)
+    n_surv = counters["table_centres"] + counters["row_centres"]
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -404,21 +422,37 @@ def main():
            "h2d_bytes_per_step": int(mask.nbytes + labels.nbytes),
            "d2h_bytes_per_step": int(2 * 4 * n_labels)}
 
-    # roofline of the dominant kernel
+    # per-kernel roofline: HBM kernels by algorithmic bytes, painting by
+    # updates per second against the probed atomic-update ceiling
     peak, peak_kind = peaks()
-    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0]),
-                   "share": v[1] / max(1e-9, sum(x[1] for x in trace.values()))}
-               for k, v in trace.items()}
+    probe = update_rate_probe(lt, dev) if rank == 0 else None
+    total_ms = sum(x[1] for x in trace.values())
+    kernels = {}
+    for k, v in trace.items():
+        avg = v[1] / max(1, v[0])
+        e = {"launches": v[0], "avg_ms": avg, "share": v[1] / max(1e-9, total_ms)}
+        ab = algorithmic_bytes(k, nvox, n_surv)
+        if ab is not None:
+            e.update({"algorithmic_bytes": ab, "achieved_gbs": ab / (avg * 1e-3) / 1e9})
+            e["frac_hbm"] = e["achieved_gbs"] / peak
+        if k == "lt_paint":
+            e.update({"updates": counters["updates"],
+                      "achieved_gupd": counters["updates"] / (avg * 1e-3) / 1e9})
+        kernels[k] = e
     dom = max(trace, key=lambda k: trace[k][1])
-    avg_ms = trace[dom][1] / trace[dom][0]
-    ab = algorithmic_bytes(dom, nvox, n_surv)
-    roof = {"kernel": dom, "bound": "hbm", "peak": peak, "unit": "GB/s",
-            "peak_source": peak_kind, "traffic": None,
-            "avg_ms": avg_ms, "achieved": None, "frac": None}
-    if ab is not None:
-        roof["achieved"] = ab / (avg_ms * 1e-3) / 1e9
-        roof["frac"] = roof["achieved"] / peak
-        roof["algorithmic_bytes"] = ab
+    kd = kernels[dom]
+    if dom == "lt_paint" and probe:
+        upeak = max(probe.values())
+        roof = {"kernel": dom, "bound": "atomic", "achieved": kd["achieved_gupd"], "peak": upeak,
+                "unit": "Gupdates/s", "frac": kd["achieved_gupd"] / upeak,
+                "traffic": TRAFFIC.get(dom), "avg_ms": kd["avg_ms"], "updates": counters["updates"],
+                "peak_source": "measured in this run by lt_probe_update_rate (best of its patterns)",
+                "probe_gupd": probe}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd.get("achieved_gbs"), "peak": peak,
+                "unit": "GB/s", "frac": kd.get("frac_hbm"), "traffic": TRAFFIC.get(dom),
+                "avg_ms": kd["avg_ms"], "algorithmic_bytes": kd.get("algorithmic_bytes"),
+                "peak_source": peak_kind}
     gpu_launches = sum(v[0] for v in trace.values())
 
     batched = None
@@ -443,6 +477,7 @@ def main():
                "data": "synthetic",
                "config": {"workload": args.workload, "voxels": nvox, "objects": n_labels - 1,
                           "foreground": float(mask.mean()), "centres_kept": n_surv,
+                          "counters": counters,
                           "seed": args.seed, "parallelism": f"replicas{world}",
                           "l2": "inputs larger than L2 (no flush needed)"},
                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,

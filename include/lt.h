@@ -26,8 +26,9 @@
  *               stream). Device-pointer calls only enqueue work and return;
  *               argument errors are returned immediately and nothing is
  *               enqueued. Errors that only the device can see (a label out of
- *               range, a labelled voxel outside the mask) are recorded in the
- *               workspace; read them with lt_workspace_status.
+ *               range, a labelled voxel outside the mask, a wait limit
+ *               reached) are recorded in the workspace; read them with
+ *               lt_workspace_status.
  *   Threads     Calls are thread-safe as long as they use distinct
  *               workspaces and outputs.
  *
@@ -64,7 +65,10 @@ typedef enum lt_status {
   LT_ERR_LABEL_RANGE = 4,         /* device-detected: a label >= n_labels */
   LT_ERR_LABEL_OUTSIDE_MASK = 5,  /* device-detected: label != 0 where mask == 0 */
   LT_ERR_CUDA = 6,                /* a CUDA call or kernel launch failed */
-  LT_ERR_NO_DEVICE = 7            /* no usable sm_103 device */
+  LT_ERR_NO_DEVICE = 7,           /* no usable sm_103 device */
+  LT_ERR_TIMEOUT = 8              /* device-detected: an asynchronous copy did not arrive
+                                     within a kernel's wait limit (the kernel stopped early;
+                                     outputs are invalid) */
 } lt_status;
 
 /* Per-object sums, one entry per label (structure of arrays, device memory).
@@ -299,6 +303,33 @@ int lt_trace_summary(lt_trace_entry* out, int max_entries);
 /* Waits for `stream`, then returns the first device-detected error recorded
  * in `ws` since the last call that used it (LT_OK if none). */
 lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream);
+
+/* Work counters of the last lt_local_thickness (or lt_measure) that used
+ * `ws`, after waiting for `stream`: centres kept by the containment test and
+ * painted from crescent tables (table_centres) or row by row (row_centres),
+ * and the LT2 updates (32-bit atomic max) the painting issued, in total and
+ * from crescent tables. */
+typedef struct lt_lt_counters {
+  uint32_t table_centres;
+  uint32_t row_centres;
+  uint64_t updates;
+  uint64_t table_updates;
+} lt_lt_counters;
+lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, lt_lt_counters* out);
+
+/* ------------------------------------------------------------ calibration --
+ * Measures this GPU's rate of 32-bit atomic-max updates to global memory,
+ * the operation the painting step consists of, as a ceiling to compare
+ * painting against. `buf` (device, `words` uint32, words a power of two
+ * >= 2^20, contents overwritten) is the target array: one larger than L2
+ * measures updates that go to HBM, a small one updates that stay in L2.
+ * pattern 0: each warp updates the 32 words of one 128-byte line per
+ *   instruction (the best case: one line per warp instruction);
+ * pattern 1: every lane updates a word in a different line (the worst case).
+ * Lines are picked by a hash, `reps` timed launches after one warm-up;
+ * writes updates per second to *rate. Synchronous (waits for `stream`). */
+lt_status lt_probe_update_rate(uint32_t* buf, size_t words, int pattern, int reps, void* stream,
+                               double* rate);
 
 #ifdef __cplusplus
 }

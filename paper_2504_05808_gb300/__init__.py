@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lt.so")
 LT_OK = 0
 STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_DIMS", 3: "LT_ERR_WORKSPACE",
                 4: "LT_ERR_LABEL_RANGE", 5: "LT_ERR_LABEL_OUTSIDE_MASK", 6: "LT_ERR_CUDA",
-                7: "LT_ERR_NO_DEVICE"}
+                7: "LT_ERR_NO_DEVICE", 8: "LT_ERR_TIMEOUT"}
 FIXED_POINT_SHIFT = 20
 MLP_FEATURES = 48
 MLP_PARAMS = 7361
@@ -44,6 +44,8 @@ SIGNATURES = {
     "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
     "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
+    "lt_workspace_counters": (_i32, [_vp, _sz, _vp, _vp]),
+    "lt_probe_update_rate": (_i32, [_vp, _sz, _i32, _i32, _vp, _vp]),
     "lt_shape_measures_static": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp]),
     "lt_features_workspace_size": (_sz, [_u32]),
     "lt_object_features": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
@@ -70,6 +72,11 @@ class LTError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
         self.status = status
+
+
+class LTCounters(ctypes.Structure):
+    _fields_ = [("table_centres", ctypes.c_uint32), ("row_centres", ctypes.c_uint32),
+                ("updates", ctypes.c_uint64), ("table_updates", ctypes.c_uint64)]
 
 
 class ObjectStats(ctypes.Structure):
@@ -213,6 +220,30 @@ def lt_trace_summary():
 
 def lt_workspace_status(ws, stream=None):
     _check(lib.lt_workspace_status(_ptr(ws), ws.numel(), _stream(stream)), "device status")
+
+
+def lt_workspace_counters(ws, stream=None):
+    """Work counters of the last local-thickness run on `ws`: dict with
+    table_centres, row_centres, updates (LT2 atomic-max updates) and
+    table_updates (those from crescent tables)."""
+    c = LTCounters()
+    _check(lib.lt_workspace_counters(_ptr(ws), ws.numel(), _stream(stream), ctypes.byref(c)),
+           "workspace counters")
+    return {"table_centres": c.table_centres, "row_centres": c.row_centres, "updates": c.updates,
+            "table_updates": c.table_updates}
+
+
+def lt_probe_update_rate(buf, pattern, reps=5, stream=None):
+    """Atomic-max updates per second this GPU sustains on `buf` (int32 CUDA
+    tensor, power-of-two length >= 2^20, overwritten); pattern 0: one
+    128-byte line per warp instruction, 1: one line per lane."""
+    import torch
+    if buf.dtype not in (torch.int32, torch.uint32):
+        raise ValueError("expected an int32 tensor")
+    rate = ctypes.c_double()
+    _check(lib.lt_probe_update_rate(_ptr(buf), buf.numel(), pattern, reps, _stream(stream),
+                                    ctypes.byref(rate)), "update-rate probe")
+    return rate.value
 
 
 # ------------------------------------------------------- learned sphericity

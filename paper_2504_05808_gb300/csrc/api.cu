@@ -132,6 +132,7 @@ const char* lt_status_string(lt_status status) {
     case LT_ERR_LABEL_OUTSIDE_MASK: return "a voxel outside the mask carries a nonzero label";
     case LT_ERR_CUDA: return "CUDA error";
     case LT_ERR_NO_DEVICE: return "no usable CUDA device";
+    case LT_ERR_TIMEOUT: return "a kernel's wait for an asynchronous copy reached its limit";
   }
   return "unknown status";
 }
@@ -283,8 +284,24 @@ lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
   uint32_t err = 0;
   if (cudaMemcpy(&err, ws, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return LT_ERR_CUDA;
+  if (err & ERR_TIMEOUT) return LT_ERR_TIMEOUT;
   if (err & ERR_LABEL_OUTSIDE_MASK) return LT_ERR_LABEL_OUTSIDE_MASK;
   if (err & ERR_LABEL_RANGE) return LT_ERR_LABEL_RANGE;
+  return LT_OK;
+}
+
+lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, lt_lt_counters* out) {
+  if (!ws || ws_bytes < sizeof(WsHeader) || !aligned(ws, kAlign)) return LT_ERR_WORKSPACE;
+  if (!out) return LT_ERR_INVALID_ARG;
+  lt_status st = use_device_of(ws);
+  if (st != LT_OK) return st;
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
+  WsHeader h;
+  if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LT_ERR_CUDA;
+  out->table_centres = h.n_surv;
+  out->row_centres = h.n_big;
+  out->updates = h.n_updates;
+  out->table_updates = h.n_table_updates;
   return LT_OK;
 }
 

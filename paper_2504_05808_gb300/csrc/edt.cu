@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict
   }
 }
 
+// Lower envelope at p. best starts at min(f(p), (p+1)^2, (L-p)^2), the last
+// two being the padding parabolas; the scan only visits k with k^2 < best,
+// hence k <= p and p + k < L: no bounds checks are needed.
 __device__ __forceinline__ uint32_t envelope_at(const uint32_t* __restrict__ col, int stride, int p,
                                                 int L) {
   uint32_t best = col[p * stride];
@@ -138,9 +141,15 @@ __device__ __forceinline__ uint32_t envelope_at(const uint32_t* __restrict__ col
   const uint32_t b1 = (uint32_t)(p + 1) * (uint32_t)(p + 1);
   const uint32_t b2 = (uint32_t)(L - p) * (uint32_t)(L - p);
   best = min(best, min(b1, b2));
-  for (uint32_t k = 1; k * k < best; ++k) {
-    if ((uint32_t)p >= k) best = min(best, col[(p - (int)k) * stride] + k * k);
-    if (p + (int)k < L) best = min(best, col[(p + (int)k) * stride] + k * k);
+  const uint32_t* lo = col + p * stride;
+  const uint32_t* hi = lo;
+  uint32_t k2 = 1, dk = 3;  // k^2 and (k+1)^2 - k^2
+  while (k2 < best) {
+    lo -= stride;
+    hi += stride;
+    best = min(best, min(*lo, *hi) + k2);
+    k2 += dk;
+    dk += 2;
   }
   return best;
 }

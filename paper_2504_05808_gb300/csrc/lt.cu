@@ -47,10 +47,14 @@
 // device into the arrays below (about 13 MiB of device memory).
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "lt_internal.cuh"
+#include "tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace ltk {
 namespace {
@@ -172,32 +176,48 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // Clears LT2, validates labels against the mask, sets the `touch` flag,
 // applies the containment test and appends kept centres.
 //
-// A CTA owns a 32 x 8 (x, y) column tile and marches along z through
-// RZ planes, keeping three halo planes (34 x 10) of (DT2, label) pairs
-// in shared memory; outside the array the halo holds (0, 0), which never
-// matches an object label. Per plane, the labelled foreground voxels are
-// compacted to the front of the CTA so that the 26-neighbour (8 in 2D) test
-// runs on full warps; every neighbour is evaluated without early exit.
-// Kept centres collect in shared memory and leave with one global atomic
-// per list every kRidgeFlush planes: centres painted from crescent tables
-// (3D, r^2 <= kCresT, with a dominant neighbour; every 2D centre) go to the
-// front of `surv`, the others (painted row by row) to the back.
+// A CTA owns a 32 x 8 (x, y) column tile and marches along z through RZ
+// planes. Halo planes of DT2 and labels (x0-4 .. x0+35, y0-1 .. y0+8) sit in
+// a ring of four shared-memory slots: planes z-1, z, z+1 are read while
+// plane z+2 is in flight. With TMA (row pitch a multiple of 16 bytes) one
+// thread issues a tiled bulk copy per plane and array, completing on the
+// slot's mbarrier, so the next plane loads while this one is tested;
+// otherwise all threads load plane z+1 with plain loads. Outside the array
+// the halo holds (0, 0), which never matches an object label. Per plane, the
+// labelled foreground voxels are compacted to the front of the CTA so that
+// the 26-neighbour (8 in 2D) test runs on full warps; every neighbour is
+// evaluated without early exit. Kept centres collect in one shared buffer
+// (table list from its front, row list from its back) and leave with one
+// global atomic per list every kRidgeFlush planes: centres painted from
+// crescent tables (3D, r^2 <= kCresT, with a dominant neighbour; every 2D
+// centre) go to the front of `surv`, the others (painted row by row) to the
+// back.
 // Record: x = linear index, y = r^2 | dominant neighbour code << 25 (code =
 // (dz+1)*9 + (dy+1)*3 + (dx+1), or 31 for none), z = codes of up to two
 // more higher-ranked same-label neighbours (5 bits each, 31 for none).
 constexpr int kTX = 32, kTY = 8;
-constexpr int kHX = kTX + 2, kHY = kTY + 2, kPlane = kHX * kHY;
+constexpr int kOX = 4;                             // halo column of x0 (keeps TMA x 16-byte aligned)
+constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 40 x 10 words
+constexpr int kSlotPitch = 416;                    // words per slot: 40 x 10 rounded up to 128 bytes
+constexpr int kSlots = 4;
 constexpr int kRidgeFlush = 2;
+constexpr int kListBuf = 256 * kRidgeFlush;
+constexpr uint32_t kPlaneBytes = kBX * kBY * 4;
+static_assert(kSlotPitch * 4 % 128 == 0 && kSlotPitch >= kBX * kBY, "slot layout");
 
-template <int NDIM, int RZ>
-__global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restrict__ dt2,
+template <int NDIM, int RZ, bool TMA>
+__global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ CUtensorMap map_dt2,
+                                                       const __grid_constant__ CUtensorMap map_lab,
+                                                       const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
                                                        uint4* __restrict__ surv,
                                                        WsHeader* __restrict__ hdr) {
-  __shared__ uint2 sDL[3][kPlane];
-  __shared__ uint4 bufA[256 * kRidgeFlush], bufB[256 * kRidgeFlush];
+  __shared__ __align__(128) uint32_t sD[kSlots][kSlotPitch];
+  __shared__ __align__(128) uint32_t sL[kSlots][kSlotPitch];
+  __shared__ uint4 buf[kListBuf];
   __shared__ uint16_t work[256];
+  __shared__ __align__(8) uint64_t bar[kSlots];
   __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s;
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -206,55 +226,93 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
   const size_t plane = (size_t)d.nx * d.ny;
   const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
   const unsigned below = (1u << lane) - 1u;
-  if (tid == 0) {
-    cntA = cntB = 0;
-    flags = 0;
-    nwork_s = 0;
-  }
-  auto load_plane = [&](int z, int slot) {
-    for (int i = tid; i < kPlane; i += 256) {
-      const int hx = i % kHX, hy = i / kHX;
+  // plane p lives in slot (p - z0 + 1) mod 4; its copy is the k-th into that
+  // slot, k = (p - z0 + 1) / 4, completing the barrier phase of parity k & 1
+  auto slot_of = [&](int p) { return (p - z0 + 1) & (kSlots - 1); };
+  auto parity_of = [&](int p) { return (uint32_t)(((p - z0 + 1) >> 2) & 1); };
+  auto issue = [&](int p) {
+    const int s = slot_of(p);
+    mbar_expect_tx(&bar[s], 2 * kPlaneBytes);
+    tma_load_3d(sD[s], &map_dt2, x0 - kOX, y0 - 1, p, &bar[s]);
+    tma_load_3d(sL[s], &map_lab, x0 - kOX, y0 - 1, p, &bar[s]);
+  };
+  auto load_plane = [&](int z) {
+    const int s = slot_of(z);
+    for (int i = tid; i < (kTX + 2) * kBY; i += 256) {
+      const int hx = i % (kTX + 2), hy = i / (kTX + 2);
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      uint2 dl = make_uint2(0u, 0u);
+      uint32_t dv = 0u, lv = 0u;
       if (z >= 0 && z < d.nz && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
         const size_t g = (size_t)z * plane + (size_t)gy * d.nx + gx;
-        dl = make_uint2(dt2[g], labels[g]);
+        dv = dt2[g];
+        lv = labels[g];
       }
-      sDL[slot][i] = dl;
+      sD[s][hy * kBX + hx + kOX - 1] = dv;
+      sL[s][hy * kBX + hx + kOX - 1] = lv;
     }
   };
-  if (NDIM == 3) {
-    load_plane(z0 - 1, (z0 + 2) % 3);
-    load_plane(z0, z0 % 3);
+  if (tid == 0) {
+    cntA = cntB = 0;
+    // after a timeout anywhere in this launch, the remaining CTAs stop at once
+    flags = TMA && (*(volatile uint32_t*)&hdr->error & ERR_TIMEOUT) ? 4u : 0u;
+    nwork_s = 0;
+    if (TMA) {
+      for (int s = 0; s < kSlots; ++s) mbar_init(&bar[s], 1);
+      fence_barrier_init();
+    }
+  }
+  __syncthreads();
+  if (flags & 4u) return;
+  if (TMA) {
+    if (tid == 0)
+      for (int p = z0 - 1; p <= min(z1, z0 + 2); ++p) issue(p);
+  } else if (NDIM == 3) {
+    load_plane(z0 - 1);
+    load_plane(z0);
   } else {
-    load_plane(-1, 2);
-    load_plane(0, 0);
-    load_plane(1, 1);
+    load_plane(-1);
+    load_plane(0);
+    load_plane(1);
   }
   for (int z = z0; z < z1; ++z) {
-    if (NDIM == 3) load_plane(z + 1, (z + 1) % 3);
-    __syncthreads();
-    const int sm = NDIM == 3 ? (z + 2) % 3 : 2, s0 = NDIM == 3 ? z % 3 : 0, sp = NDIM == 3 ? (z + 1) % 3 : 1;
+    bool ok = true;
+    if (TMA) {
+      if (z == z0) ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1)) && mbar_wait(&bar[slot_of(z)], parity_of(z));
+      ok = ok && mbar_wait(&bar[slot_of(z + 1)], parity_of(z + 1));
+    } else if (NDIM == 3) {
+      load_plane(z + 1);
+    }
+    if (__syncthreads_or(!ok)) {
+      // a copy did not arrive within the wait limit: record it, wait (again
+      // bounded) for the copies this CTA still has in flight, and stop
+      if (tid == 0) {
+        atomicOr(&hdr->error, ERR_TIMEOUT);
+        for (int p = z - 1; p <= min(z1, z + 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p));
+      }
+      return;
+    }
+    const uint32_t* Dm = sD[slot_of(z - 1)];
+    const uint32_t* D0 = sD[slot_of(z)];
+    const uint32_t* Dp = sD[slot_of(z + 1)];
+    const uint32_t* Lm = sL[slot_of(z - 1)];
+    const uint32_t* L0 = sL[slot_of(z)];
+    const uint32_t* Lp = sL[slot_of(z + 1)];
     // pass 1, every voxel of the tile: clear LT2, flags, compaction
     {
       const int tx = tid & 31, ty = tid >> 5;
       const int x = x0 + tx, y = y0 + ty;
       const bool in = x < d.nx && y < d.ny;
-      const int c = (ty + 1) * kHX + (tx + 1);
-      const uint2 me = sDL[s0][c];
+      const int c = (ty + 1) * kBX + (tx + kOX);
+      const uint32_t md = D0[c], ml = L0[c];
       bool isw = false, touch = false, bad = false;
       if (in) {
         lt2[(size_t)z * plane + (size_t)y * d.nx + x] = 0u;
-        bad = me.x == 0 && me.y != 0;
-        if (me.x != 0) {
-          const uint2 ex = sDL[s0][c + 1], ey = sDL[s0][c + kHX];
-          touch = (ex.x && ex.y != me.y) || (ey.x && ey.y != me.y);
-          if (NDIM == 3) {
-            const uint2 ez = sDL[sp][c];
-            touch = touch || (ez.x && ez.y != me.y);
-          }
+        bad = md == 0 && ml != 0;
+        if (md != 0) {
+          touch = (D0[c + 1] && L0[c + 1] != ml) || (D0[c + kBX] && L0[c + kBX] != ml);
+          if (NDIM == 3) touch = touch || (Dp[c] && Lp[c] != ml);
         }
-        isw = me.x != 0 && me.y != 0;
+        isw = md != 0 && ml != 0;
       }
       if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
       if (__any_sync(kFull, touch) && lane == 0) atomicOr(&flags, 2u);
@@ -272,9 +330,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
     if ((uint32_t)tid < nwork) {
       const int t = work[tid];
       const int tx = t & 31, ty = t >> 5;
-      const int c = (ty + 1) * kHX + (tx + 1);
-      const uint2 me = sDL[s0][c];
-      const uint32_t r2 = me.x, l = me.y;
+      const int c = (ty + 1) * kBX + (tx + kOX);
+      const uint32_t r2 = D0[c], l = L0[c];
       int m[3] = {kNoTable, kNoTable, kNoTable};
       if (r2 <= kMCap) {
         m[0] = (int)mt[r2];
@@ -287,17 +344,19 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
       uint32_t kmax[3] = {0u, 0u, 0u};
 #pragma unroll
       for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
-        const int slot = dz < 0 ? sm : (dz == 0 ? s0 : sp);
+        const uint32_t* Dz = dz < 0 ? Dm : (dz == 0 ? D0 : Dp);
+        const uint32_t* Lz = dz < 0 ? Lm : (dz == 0 ? L0 : Lp);
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx) {
             if (dx == 0 && dy == 0 && dz == 0) continue;
-            const uint2 nb = sDL[slot][c + dy * kHX + dx];
+            const int h = c + dy * kBX + dx;
+            const uint32_t nd = Dz[h], nl = Lz[h];
             const int k = (dx != 0) + (dy != 0) + (dz != 0) - 1;
             const uint32_t pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-            const uint32_t key = (nb.x << 6) | (pos << 5) | (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-            kmax[k] = max(kmax[k], nb.y == l ? key : 0u);
+            const uint32_t key = (nd << 6) | (pos << 5) | (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+            kmax[k] = max(kmax[k], nl == l ? key : 0u);
           }
         }
       }
@@ -354,20 +413,26 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
         keepB = !tab;
       }
     }
+    // at most 256 * kRidgeFlush records between flushes: list A grows from
+    // the front of buf, list B from its back
     const unsigned ba = __ballot_sync(kFull, keepA), bb = __ballot_sync(kFull, keepB);
     if (ba) {
       uint32_t wb = 0;
       if (lane == 0) wb = atomicAdd(&cntA, (uint32_t)__popc(ba));
       wb = __shfl_sync(kFull, wb, 0);
-      if (keepA) bufA[wb + __popc(ba & below)] = rec;
+      if (keepA) buf[wb + __popc(ba & below)] = rec;
     }
     if (bb) {
       uint32_t wb = 0;
       if (lane == 0) wb = atomicAdd(&cntB, (uint32_t)__popc(bb));
       wb = __shfl_sync(kFull, wb, 0);
-      if (keepB) bufB[wb + __popc(bb & below)] = rec;
+      if (keepB) buf[kListBuf - 1 - (wb + __popc(bb & below))] = rec;
     }
-    __syncthreads();  // plane z-1 is free again; the buffers may be flushed
+    __syncthreads();  // plane z-1 is free again; the buffer may be flushed
+    if (TMA && tid == 0 && z + 3 <= z1) {
+      fence_proxy_async();
+      issue(z + 3);
+    }
     if (tid == 0) nwork_s = 0;
     if ((z - z0) % kRidgeFlush == kRidgeFlush - 1 || z + 1 == z1) {
       if (tid == 0) {
@@ -375,8 +440,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const uint32_t* __restric
         baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
       }
       __syncthreads();
-      for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = bufA[i];
-      for (uint32_t i = tid; i < cntB; i += 256) surv[(size_t)d.n - 1 - (baseB + i)] = bufB[i];
+      for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = buf[i];
+      for (uint32_t i = tid; i < cntB; i += 256) surv[(size_t)d.n - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
       __syncthreads();
       if (tid == 0) cntA = cntB = 0;
     }
@@ -409,12 +474,13 @@ __device__ __forceinline__ void paint_span(const Centre& c, int a, int b, int w,
                                            size_t rowbase, bool touch,
                                            const uint32_t* __restrict__ dt2,
                                            const uint32_t* __restrict__ labels,
-                                           uint32_t* __restrict__ lt2) {
+                                           uint32_t* __restrict__ lt2, uint32_t& nupd) {
   for (int dx = a; dx <= b; ++dx) {
     const size_t i = rowbase + (size_t)(c.cx + dx);
     if (exact && (dx == w || dx == -w) && dt2[i] == 0) continue;
     if (touch && labels[i] != c.label) continue;
     atomicMax(lt2 + i, c.r2);
+    ++nupd;
   }
 }
 
@@ -423,7 +489,7 @@ __device__ __forceinline__ void paint_span(const Centre& c, int a, int b, int w,
 __device__ __forceinline__ void paint_rows(const Centre& c, int dz, int seg, const Dims& d, size_t sy,
                                            size_t sz, bool touch, const uint32_t* __restrict__ dt2,
                                            const uint32_t* __restrict__ labels,
-                                           uint32_t* __restrict__ lt2) {
+                                           uint32_t* __restrict__ lt2, uint32_t& nupd) {
   const int z = c.cz + dz;
   if (z < 0 || z >= d.nz) return;
   const int hz2 = (int)c.r2 - dz * dz;
@@ -451,8 +517,8 @@ __device__ __forceinline__ void paint_rows(const Centre& c, int dz, int seg, con
     }
     const bool exact = wr * wr == h;
     const size_t rowbase = (size_t)z * sz + (size_t)y * sy;
-    paint_span(c, max(-wr, xmin), min(hi1, xmax), wr, exact, rowbase, touch, dt2, labels, lt2);
-    paint_span(c, max(lo2, xmin), min(hi2, xmax), wr, exact, rowbase, touch, dt2, labels, lt2);
+    paint_span(c, max(-wr, xmin), min(hi1, xmax), wr, exact, rowbase, touch, dt2, labels, lt2, nupd);
+    paint_span(c, max(lo2, xmin), min(hi2, xmax), wr, exact, rowbase, touch, dt2, labels, lt2, nupd);
   }
 }
 
@@ -460,7 +526,7 @@ __device__ __forceinline__ void paint_rows(const Centre& c, int dz, int seg, con
 __device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, const Dims& d, bool touch,
                                                   const uint32_t* __restrict__ dt2,
                                                   const uint32_t* __restrict__ labels,
-                                                  uint32_t* __restrict__ lt2) {
+                                                  uint32_t* __restrict__ lt2, uint32_t& nupd) {
   const uint32_t p = g_cres_vox[c.vstart + t];
   const int o0 = (int)(p & 0xFFu) - 128, o1 = (int)((p >> 8) & 0xFFu) - 128,
             o2 = (int)((p >> 16) & 0xFFu) - 128;
@@ -484,6 +550,7 @@ __device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, c
   if ((p >> 24) && dt2[i] == 0) return;
   if (touch && labels[i] != c.label) return;
   atomicMax(lt2 + i, c.r2);
+  ++nupd;
 }
 
 // Decodes a centre record; returns its number of work items: crescent voxels
@@ -565,14 +632,14 @@ template <int NDIM>
 __device__ __forceinline__ void paint_row_item(const Centre& c, int local, const Dims& d, size_t sy,
                                                size_t sz, bool touch, const uint32_t* __restrict__ dt2,
                                                const uint32_t* __restrict__ labels,
-                                               uint32_t* __restrict__ lt2) {
+                                               uint32_t* __restrict__ lt2, uint32_t& nupd) {
   if (NDIM == 3) {
     int q = (int)((float)local * c.inv_nseg);
     if (q * c.nseg > local) --q;
     else if ((q + 1) * c.nseg <= local) ++q;
-    paint_rows(c, q - c.R, local - q * c.nseg, d, sy, sz, touch, dt2, labels, lt2);
+    paint_rows(c, q - c.R, local - q * c.nseg, d, sy, sz, touch, dt2, labels, lt2, nupd);
   } else {
-    paint_rows(c, 0, local, d, sy, sz, touch, dt2, labels, lt2);
+    paint_rows(c, 0, local, d, sy, sz, touch, dt2, labels, lt2, nupd);
   }
 }
 
@@ -595,6 +662,7 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   const uint32_t nbig = *(volatile uint32_t*)&hdr->n_big;
   const bool touch = *(volatile uint32_t*)&hdr->touch != 0;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  uint32_t nupd = 0, ntab = 0;  // updates this thread issued: row by row, from tables
   if (NDIM == 3) {
     for (;;) {
       uint32_t b = 0;
@@ -603,7 +671,7 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
       if (b >= nbig) break;
       Centre c;
       const int items = make_centre<NDIM>(surv[(size_t)d.n - 1 - b], false, d, sy, sz, touch, dt2, labels, c);
-      for (int k = lane; k < items; k += 32) paint_row_item<NDIM>(c, k, d, sy, sz, touch, dt2, labels, lt2);
+      for (int k = lane; k < items; k += 32) paint_row_item<NDIM>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
     }
   }
   const uint32_t nchunks = (n + 31) / 32;
@@ -641,15 +709,54 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
       const Centre& c = cs[w][j];
       const int local = k - c.start;
       if (c.mode)
-        paint_table_voxel(c, (uint32_t)local, d, touch, dt2, labels, lt2);
+        paint_table_voxel(c, (uint32_t)local, d, touch, dt2, labels, lt2, ntab);
       else
-        paint_row_item<NDIM>(c, local, d, sy, sz, touch, dt2, labels, lt2);
+        paint_row_item<NDIM>(c, local, d, sy, sz, touch, dt2, labels, lt2, nupd);
     }
     __syncwarp();
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    nupd += __shfl_xor_sync(kFull, nupd, o);
+    ntab += __shfl_xor_sync(kFull, ntab, o);
+  }
+  if (lane == 0 && nupd + ntab) {
+    atomicAdd(&hdr->n_updates, (unsigned long long)(nupd + ntab));
+    atomicAdd(&hdr->n_table_updates, (unsigned long long)ntab);
+  }
+}
+
+template <int NDIM, int RZ>
+void launch_ridge(bool tma, dim3 grid, cudaStream_t s, const CUtensorMap& md, const CUtensorMap& ml,
+                  const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d, uint4* surv,
+                  WsHeader* hdr) {
+  if (tma)
+    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr);
+  else
+    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr);
 }
 
 }  // namespace
+
+bool make_tensor_map_u32_3d(CUtensorMap* map, const void* base, int nx, int ny, int nz, int bx, int by) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || (reinterpret_cast<uintptr_t>(base) & 15u) || (nx * 4) % 16) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint4)); }
 
@@ -662,16 +769,22 @@ cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2
   uint4* surv = reinterpret_cast<uint4*>(body);
   const int rz = tu.ridge_z == 8 || tu.ridge_z == 32 ? tu.ridge_z : 16;
   dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY, d.ndim == 3 ? (d.nz + rz - 1) / rz : 1);
+  // TMA needs a row pitch that is a multiple of 16 bytes
+  CUtensorMap md, ml;
+  std::memset(&md, 0, sizeof(md));
+  std::memset(&ml, 0, sizeof(ml));
+  const bool tma = d.nx % 4 == 0 && make_tensor_map_u32_3d(&md, dt2, d.nx, d.ny, d.nz, kBX, kBY) &&
+                   make_tensor_map_u32_3d(&ml, labels, d.nx, d.ny, d.nz, kBX, kBY);
   {
     TraceScope t("lt_ridge", s);
     if (d.ndim == 2)
-      lt_ridge_kernel<2, 16><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<2, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
     else if (rz == 8)
-      lt_ridge_kernel<3, 8><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 8>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
     else if (rz == 32)
-      lt_ridge_kernel<3, 32><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 32>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
     else
-      lt_ridge_kernel<3, 16><<<grid, 256, 0, s>>>(dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -25,11 +25,13 @@ struct WsHeader {
   uint32_t n_surv;  // kept centres painted from crescent tables (list from the front)
   uint32_t n_big;   // kept centres painted row by row (list from the back)
   uint32_t ctr_small, ctr_big;  // work counters of the paint kernel
-  uint32_t reserved[58];
+  unsigned long long n_updates;        // LT2 updates (atomic max) the paint kernel issued
+  unsigned long long n_table_updates;  // of which from crescent tables
+  uint32_t reserved[54];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
-enum : uint32_t { ERR_LABEL_RANGE = 1u, ERR_LABEL_OUTSIDE_MASK = 2u };
+enum : uint32_t { ERR_LABEL_RANGE = 1u, ERR_LABEL_OUTSIDE_MASK = 2u, ERR_TIMEOUT = 4u };
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lt):
 
 
 def test_status_strings_and_version(lt):
-    for code in range(8):
+    for code in range(9):
         s = lt.lib.lt_status_string(code)
         assert s and s != b"unknown status"
     assert lt.lib.lt_status_string(99) == b"unknown status"
