@@ -63,7 +63,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kMCap = 1u << 18;  // containment table covers r^2 <= 2^18
 constexpr int kCresT = 144;           // crescent tables cover r^2 <= 144
 constexpr int kCresMaxCombos = 12288;
-constexpr int kCresMaxVoxels = 1 << 21;
+constexpr int kCresMaxVoxels = 2304 * 1024;  // both orderings (about 2.16 M voxels)
 constexpr uint32_t kNoDominant = 31u;
 constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 
@@ -71,13 +71,16 @@ __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
 __device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
 __device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
 __device__ uint32_t g_cres_start[kCresMaxCombos + 1];
+// the same crescents with another canonical axis innermost: y for class 1,
+// z for class 2 (class 3: same as g_cres_start); the size is the same
+__device__ uint32_t g_cres_start_alt[kCresMaxCombos];
 // canonical crescent voxels: (x+128) | (y+128) << 8 | (z+128) << 16 |
 // (on the sphere |y|^2 == r^2) << 24
 __device__ uint32_t g_cres_vox[kCresMaxVoxels];
 
 // ------------------------------------------------------------ host tables
 struct HostTables {
-  std::vector<uint32_t> m3, m2, base, start, vox;
+  std::vector<uint32_t> m3, m2, base, start, start_alt, vox;
   bool ok = false;
 };
 
@@ -116,31 +119,53 @@ HostTables* build_host_tables() {
   for (int k = 0; k < 2; ++k)
     for (uint32_t n = 1; n <= cap; ++n)
       t->m2[k * (size_t)(cap + 1) + n] = std::max(t->m2[k * (size_t)(cap + 1) + n], t->m2[k * (size_t)(cap + 1) + n - 1]);
-  // crescents B(0, r^2) \ B(d, rd^2) for the canonical offsets
+  // crescents B(0, r^2) \ B(d, rd^2) for the canonical offsets, canonical
+  // x innermost; then classes 1 and 2 again with canonical y (class 1) or z
+  // (class 2) innermost, the axis that is world x when the offset has no x
+  // component, so that consecutive voxels run along memory rows
   const int dl[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 1, 1}};
+  auto crescent = [&](int k, int r2, uint32_t rd2, int inner) {
+    const int Rr = isqrt_host(r2);
+    for (int u = -Rr; u <= Rr; ++u)
+      for (int v = -Rr; v <= Rr; ++v)
+        for (int w = -Rr; w <= Rr; ++w) {
+          int c[3];  // canonical x, y, z; w runs along axis `inner`
+          c[inner] = w;
+          c[inner == 0 ? 1 : 0] = v;
+          c[inner == 2 ? 1 : 2] = u;
+          const int n = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+          if (n > r2) continue;
+          const int e = (c[0] - dl[k][0]) * (c[0] - dl[k][0]) + (c[1] - dl[k][1]) * (c[1] - dl[k][1]) +
+                        (c[2] - dl[k][2]) * (c[2] - dl[k][2]);
+          if (e <= (int)rd2) continue;
+          t->vox.push_back((uint32_t)(c[0] + 128) | ((uint32_t)(c[1] + 128) << 8) |
+                           ((uint32_t)(c[2] + 128) << 16) | ((n == r2 ? 1u : 0u) << 24));
+        }
+  };
   t->base.assign(3 * (kCresT + 1), 0u);
   for (int k = 0; k < 3; ++k)
     for (int r2 = 0; r2 <= kCresT; ++r2) {
       t->base[k * (kCresT + 1) + r2] = (uint32_t)t->start.size();
-      const int Rr = isqrt_host(r2);
       const uint32_t mlim = t->m3[k * (size_t)(cap + 1) + r2];
       for (uint32_t rd2 = (uint32_t)r2; rd2 < mlim; ++rd2) {
         t->start.push_back((uint32_t)t->vox.size());
-        for (int z = -Rr; z <= Rr; ++z)
-          for (int y = -Rr; y <= Rr; ++y)
-            for (int x = -Rr; x <= Rr; ++x) {
-              const int n = x * x + y * y + z * z;
-              if (n > r2) continue;
-              const int e = (x - dl[k][0]) * (x - dl[k][0]) + (y - dl[k][1]) * (y - dl[k][1]) +
-                            (z - dl[k][2]) * (z - dl[k][2]);
-              if (e <= (int)rd2) continue;
-              t->vox.push_back((uint32_t)(x + 128) | ((uint32_t)(y + 128) << 8) |
-                               ((uint32_t)(z + 128) << 16) | ((n == r2 ? 1u : 0u) << 24));
-            }
+        crescent(k, r2, rd2, 0);
       }
     }
-  t->start.push_back((uint32_t)t->vox.size());
+  t->start.push_back((uint32_t)t->vox.size());  // end of the last crescent
+  t->start_alt.assign(t->start.begin(), t->start.end() - 1);
+  for (int k = 0; k < 2; ++k)
+    for (int r2 = 0; r2 <= kCresT; ++r2) {
+      const uint32_t mlim = t->m3[k * (size_t)(cap + 1) + r2];
+      for (uint32_t rd2 = (uint32_t)r2; rd2 < mlim; ++rd2) {
+        t->start_alt[t->base[k * (kCresT + 1) + r2] + (rd2 - r2)] = (uint32_t)t->vox.size();
+        crescent(k, r2, rd2, k == 0 ? 1 : 2);
+      }
+    }
   t->ok = t->start.size() <= (size_t)kCresMaxCombos + 1 && t->vox.size() <= (size_t)kCresMaxVoxels;
+  // table records hold a crescent's first voxel in 22 bits and its size in 10
+  for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 1024u;
+  t->ok = t->ok && t->vox.size() < (1u << 22);
   return t;
 }
 
@@ -163,6 +188,7 @@ cudaError_t ensure_tables() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_m2, h.m2.data(), h.m2.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_base, h.base.data(), h.base.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_start, h.start.data(), h.start.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_start_alt, h.start_alt.data(), h.start_alt.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_vox, h.vox.data(), h.vox.size() * 4);
   if (e == cudaSuccess) g_tables_on[dev] = true;
   return e;
@@ -192,9 +218,14 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // crescent tables (3D, r^2 <= kCresT, with a dominant neighbour; every 2D
 // centre) go to the front of `surv`, the others (painted row by row) to the
 // back.
-// Record: x = linear index, y = r^2 | dominant neighbour code << 25 (code =
-// (dz+1)*9 + (dy+1)*3 + (dx+1), or 31 for none), z = codes of up to two
-// more higher-ranked same-label neighbours (5 bits each, 31 for none).
+// Records (uint4). Offset codes: (dz+1)*9 + (dy+1)*3 + (dx+1), 31 for none.
+//   Table centres (3D): x = linear index; y = first crescent voxel | crescent
+//   size << 22; z = r^2 | dominant code << 8 | codes of up to two more
+//   higher-ranked same-label neighbours << 13 (5 bits each) | ball inside
+//   the array << 23; w = those two neighbours' r^2 (8 bits each, 0xFF none).
+//   Painting needs no other lookup.
+//   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
+//   z = the two extra codes.
 constexpr int kTX = 32, kTY = 8;
 constexpr int kOX = 4;                             // halo column of x0 (keeps TMA x 16-byte aligned)
 constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 40 x 10 words
@@ -372,18 +403,18 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
         }
       }
       if (!pruned) {
-        uint32_t code = kNoDominant;
+        uint32_t code = kNoDominant, bcomb = 0, best = UINT_MAX;
         int kd = -1;
         if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
           // the candidate whose crescent has the fewest voxels
-          uint32_t best = UINT_MAX;
 #pragma unroll
           for (int k = 0; k < 3; ++k)
             if (brn[k] >= 0) {
               const uint32_t cb = cres_combo(k, r2, (uint32_t)brn[k]);
-              const uint32_t sz = g_cres_start[cb + 1] - g_cres_start[cb];
+              const uint32_t s0 = g_cres_start[cb], sz = g_cres_start[cb + 1] - s0;
               if (sz < best) {
                 best = sz;
+                bcomb = cb;
                 code = bcode[k];
                 kd = k;
               }
@@ -399,16 +430,28 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
             }
         }
         const uint32_t v = (uint32_t)((size_t)z * plane + (size_t)(y0 + ty) * d.nx + (x0 + tx));
-        // the other classes' candidates: extra balls a crescent voxel may lie in
-        uint32_t extra = kNoDominant | (kNoDominant << 5), ne = 0;
+        // the other classes' candidates: extra balls a crescent voxel may lie
+        // in, with their r^2 (below M(d, r^2) <= 188 for table centres)
+        uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0xFFFFu, ne = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
           if (NDIM == 3 && k != kd && brn[k] >= 0 && ne < 2) {
             extra = (extra & ~(31u << (5 * ne))) | (bcode[k] << (5 * ne));
+            er = (er & ~(0xFFu << (8 * ne))) | ((uint32_t)min(brn[k], 0xFE) << (8 * ne));
             ++ne;
           }
-        rec = make_uint4(v, r2 | (code << 25), extra, 0u);
         const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
+        if (NDIM == 3 && tab) {
+          // crescent order with world x innermost: the alternative order
+          // when the dominant offset has no x component
+          const uint32_t vstart = code % 3 == 1 ? g_cres_start_alt[bcomb] : g_cres_start[bcomb];
+          const int R = (int)isqrt24(r2);
+          const int x = x0 + tx, y = y0 + ty;
+          const uint32_t inside = x >= R && x + R < d.nx && y >= R && y + R < d.ny && z >= R && z + R < d.nz;
+          rec = make_uint4(v, vstart | (best << 22), r2 | (code << 8) | (extra << 13) | (inside << 23), er);
+        } else {
+          rec = make_uint4(v, r2 | (code << 25), extra, 0u);
+        }
         keepA = tab;
         keepB = !tab;
       }
@@ -459,12 +502,6 @@ struct Centre {
   int ddx, ddy, ddz, r2d;  // dominant neighbour offset and its r^2 (-1: none)
   int start, nseg;         // first item of this centre in the chunk; dy segments
   float inv_nseg;
-  uint32_t vstart;  // table mode: first crescent voxel
-  int mode;         // 0 rows; 1 table; 3 table, ball inside the array
-  int S[3];         // linear stride of canonical axes x, y, z
-  uint32_t axes;    // world axis (2 bits each) and sign bit of canonical x, y, z
-  int eoff[2];      // extra higher-ranked balls: canonical offset, 2 bits per axis
-  int er2[2];       // and their r^2 (-1: none)
 };
 constexpr int kRowSeg = 8;  // rows per row-mode work item
 
@@ -522,43 +559,12 @@ __device__ __forceinline__ void paint_rows(const Centre& c, int dz, int seg, con
   }
 }
 
-// Table mode: crescent voxel t of the centre, mapped from the canonical frame.
-__device__ __forceinline__ void paint_table_voxel(const Centre& c, uint32_t t, const Dims& d, bool touch,
-                                                  const uint32_t* __restrict__ dt2,
-                                                  const uint32_t* __restrict__ labels,
-                                                  uint32_t* __restrict__ lt2, uint32_t& nupd) {
-  const uint32_t p = g_cres_vox[c.vstart + t];
-  const int o0 = (int)(p & 0xFFu) - 128, o1 = (int)((p >> 8) & 0xFFu) - 128,
-            o2 = (int)((p >> 16) & 0xFFu) - 128;
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-    if (c.er2[q] >= 0) {  // inside another higher-ranked same-label ball: covered there
-      const int e0 = (c.eoff[q] & 3) - 1, e1 = ((c.eoff[q] >> 2) & 3) - 1, e2 = ((c.eoff[q] >> 4) & 3) - 1;
-      if ((o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= c.er2[q]) return;
-    }
-  if (!(c.mode & 2)) {  // ball may leave the array: check each coordinate
-    const int a0 = c.axes & 3, a1 = (c.axes >> 2) & 3, a2 = (c.axes >> 4) & 3;
-    const int v0 = (c.axes >> 6) & 1 ? -o0 : o0, v1 = (c.axes >> 7) & 1 ? -o1 : o1,
-              v2 = (c.axes >> 8) & 1 ? -o2 : o2;
-    const int x = c.cx + (a0 == 0 ? v0 : 0) + (a1 == 0 ? v1 : 0) + (a2 == 0 ? v2 : 0);
-    const int y = c.cy + (a0 == 1 ? v0 : 0) + (a1 == 1 ? v1 : 0) + (a2 == 1 ? v2 : 0);
-    const int z = c.cz + (a0 == 2 ? v0 : 0) + (a1 == 2 ? v1 : 0) + (a2 == 2 ? v2 : 0);
-    if (x < 0 || x >= d.nx || y < 0 || y >= d.ny || z < 0 || z >= d.nz) return;
-  }
-  const size_t i = (size_t)((int64_t)c.idx + (int64_t)o0 * c.S[0] + (int64_t)o1 * c.S[1] +
-                            (int64_t)o2 * c.S[2]);
-  if ((p >> 24) && dt2[i] == 0) return;
-  if (touch && labels[i] != c.label) return;
-  atomicMax(lt2 + i, c.r2);
-  ++nupd;
-}
-
-// Decodes a centre record; returns its number of work items: crescent voxels
-// in table mode, (2R+1) * ceil((2R+1)/8) row segments in 3D row mode and
+// Decodes a row-mode record (3D row centres, every 2D centre); returns its
+// number of work items: (2R+1) * ceil((2R+1)/8) row segments in 3D,
 // ceil((2R+1)/8) in 2D.
 template <int NDIM>
-__device__ __forceinline__ int make_centre(uint4 rec, bool table, const Dims& d, size_t sy, size_t sz,
-                                           bool touch, const uint32_t* __restrict__ dt2,
+__device__ __forceinline__ int make_centre(uint4 rec, const Dims& d, size_t sy, size_t sz, bool touch,
+                                           const uint32_t* __restrict__ dt2,
                                            const uint32_t* __restrict__ labels, Centre& c) {
   const uint32_t idx = rec.x, code = rec.y >> 25;
   c.idx = idx;
@@ -569,13 +575,7 @@ __device__ __forceinline__ int make_centre(uint4 rec, bool table, const Dims& d,
   c.cz = (int)(t / (uint32_t)d.ny);
   c.R = (int)isqrt24(c.r2);
   c.label = touch ? labels[idx] : 0u;
-  c.mode = 0;
-  c.vstart = 0;
-  c.axes = 0;
-  c.S[0] = c.S[1] = c.S[2] = 0;
   c.start = 0;
-  c.eoff[0] = c.eoff[1] = 0;
-  c.er2[0] = c.er2[1] = -1;
   if (code != kNoDominant) {
     c.ddz = (int)(code / 9) - 1;
     c.ddy = (int)(code / 3 % 3) - 1;
@@ -587,44 +587,95 @@ __device__ __forceinline__ int make_centre(uint4 rec, bool table, const Dims& d,
   }
   c.nseg = (2 * c.R + kRowSeg) / kRowSeg;
   c.inv_nseg = 1.0f / (float)c.nseg;
-  if (NDIM == 3 && table) {
-    // canonical x, y, z -> the nonzero axes of the offset first (in x, y,
-    // z order), then the zero axes
-    const int cls = (c.ddx != 0) + (c.ddy != 0) + (c.ddz != 0);
-    int a0 = 0, a1 = 1, a2 = 2;
-    if (cls == 2) {
-      if (c.ddx == 0) { a0 = 1; a1 = 2; a2 = 0; }
-      else if (c.ddy == 0) { a0 = 0; a1 = 2; a2 = 1; }
-    } else if (cls == 1) {
-      if (c.ddy != 0) { a0 = 1; a1 = 0; a2 = 2; }
-      else if (c.ddz != 0) { a0 = 2; a1 = 0; a2 = 1; }
-    }
-    auto comp = [&](int a) { return a == 0 ? c.ddx : (a == 1 ? c.ddy : c.ddz); };
-    auto stride = [&](int a) { return a == 0 ? 1LL : (a == 1 ? (long long)sy : (long long)sz); };
-    const int g0 = comp(a0) < 0, g1 = comp(a1) < 0, g2 = comp(a2) < 0;
-    c.axes = (uint32_t)(a0 | (a1 << 2) | (a2 << 4) | (g0 << 6) | (g1 << 7) | (g2 << 8));
-    c.S[0] = (int)(g0 ? -stride(a0) : stride(a0));
-    c.S[1] = (int)(g1 ? -stride(a1) : stride(a1));
-    c.S[2] = (int)(g2 ? -stride(a2) : stride(a2));
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const uint32_t ec = (rec.z >> (5 * q)) & 31u;
-      if (ec == kNoDominant) continue;
-      const int ez = (int)(ec / 9) - 1, ey = (int)(ec / 3 % 3) - 1, ex = (int)(ec % 3) - 1;
-      c.er2[q] = (int)dt2[(int64_t)idx + ez * (int64_t)sz + ey * (int64_t)sy + ex];
-      auto wcomp = [&](int a) { return a == 0 ? ex : (a == 1 ? ey : ez); };
-      const int q0 = g0 ? -wcomp(a0) : wcomp(a0), q1 = g1 ? -wcomp(a1) : wcomp(a1),
-                q2 = g2 ? -wcomp(a2) : wcomp(a2);
-      c.eoff[q] = (q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4);
-    }
-    const uint32_t cb = cres_combo(cls - 1, c.r2, (uint32_t)c.r2d);
-    c.vstart = g_cres_start[cb];
-    const bool inside = c.cx - c.R >= 0 && c.cx + c.R < d.nx && c.cy - c.R >= 0 && c.cy + c.R < d.ny &&
-                        c.cz - c.R >= 0 && c.cz + c.R < d.nz;
-    c.mode = inside ? 3 : 1;
-    return (int)(g_cres_start[cb + 1] - c.vstart);
-  }
   return (NDIM == 3 ? 2 * c.R + 1 : 1) * c.nseg;
+}
+
+// Table mode: a 3D centre with r^2 <= kCresT and a dominant neighbour,
+// decoded from its record alone (40 bytes, shared memory).
+struct TabCentre {
+  uint32_t idx, vstart, r2, label;
+  int S[3];       // signed linear strides of the canonical axes x, y, z
+  uint32_t ex;    // extra balls: r^2 (8 bits each, 0xFF none) | canonical offsets << 16 (6 bits each)
+  uint32_t axes;  // world axis (2 bits each) and sign bit (<< 6..8) of canonical x, y, z; inside << 9
+  int start;      // first crescent voxel of this centre in the chunk
+};
+
+// Canonical x, y, z of a crescent: the nonzero axes of the dominant offset
+// first (in x, y, z order), then the zero axes; signs make the offset
+// (1,0,0), (1,1,0) or (1,1,1). Returns the crescent size.
+__device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, bool touch,
+                                               const uint32_t* __restrict__ labels, TabCentre& c) {
+  c.idx = rec.x;
+  c.vstart = rec.y & 0x3FFFFFu;
+  c.r2 = rec.z & 0xFFu;
+  const uint32_t code = (rec.z >> 8) & 31u;
+  const int ddz = (int)(code / 9) - 1, ddy = (int)(code / 3 % 3) - 1, ddx = (int)(code % 3) - 1;
+  const int cls = (ddx != 0) + (ddy != 0) + (ddz != 0);
+  int a0 = 0, a1 = 1, a2 = 2;
+  if (cls == 2) {
+    if (ddx == 0) { a0 = 1; a1 = 2; a2 = 0; }
+    else if (ddy == 0) { a0 = 0; a1 = 2; a2 = 1; }
+  } else if (cls == 1) {
+    if (ddy != 0) { a0 = 1; a1 = 0; a2 = 2; }
+    else if (ddz != 0) { a0 = 2; a1 = 0; a2 = 1; }
+  }
+  auto comp = [](int a, int vx, int vy, int vz) { return a == 0 ? vx : (a == 1 ? vy : vz); };
+  const int sy_ = (int)sy, sz_ = (int)sz;
+  const int g0 = comp(a0, ddx, ddy, ddz) < 0, g1 = comp(a1, ddx, ddy, ddz) < 0, g2 = comp(a2, ddx, ddy, ddz) < 0;
+  c.axes = (uint32_t)(a0 | (a1 << 2) | (a2 << 4) | (g0 << 6) | (g1 << 7) | (g2 << 8)) | (((rec.z >> 23) & 1u) << 9);
+  const int t0 = comp(a0, 1, sy_, sz_), t1 = comp(a1, 1, sy_, sz_), t2 = comp(a2, 1, sy_, sz_);
+  c.S[0] = g0 ? -t0 : t0;
+  c.S[1] = g1 ? -t1 : t1;
+  c.S[2] = g2 ? -t2 : t2;
+  uint32_t ex = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint32_t ec = (rec.z >> (13 + 5 * q)) & 31u;
+    uint32_t er = (rec.w >> (8 * q)) & 0xFFu, eo = 0;
+    if (ec == kNoDominant) {
+      er = 0xFFu;
+    } else {
+      const int ez = (int)(ec / 9) - 1, ey = (int)(ec / 3 % 3) - 1, exx = (int)(ec % 3) - 1;
+      const int q0 = g0 ? -comp(a0, exx, ey, ez) : comp(a0, exx, ey, ez);
+      const int q1 = g1 ? -comp(a1, exx, ey, ez) : comp(a1, exx, ey, ez);
+      const int q2 = g2 ? -comp(a2, exx, ey, ez) : comp(a2, exx, ey, ez);
+      eo = (uint32_t)((q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4));
+    }
+    ex |= (er << (8 * q)) | (eo << (16 + 6 * q));
+  }
+  c.ex = ex;
+  c.label = touch ? labels[c.idx] : 0u;
+  return (int)(rec.y >> 22);
+}
+
+// Linear index of canonical crescent voxel p of c; false when the voxel lies
+// in one of c's extra higher-ranked balls (it is covered there) or outside
+// the array.
+__device__ __forceinline__ bool tab_voxel_index(const TabCentre& c, uint32_t p, const Dims& d, uint32_t& i) {
+  const int o0 = (int)(p & 0xFFu) - 128, o1 = (int)((p >> 8) & 0xFFu) - 128,
+            o2 = (int)((p >> 16) & 0xFFu) - 128;
+  const uint32_t ex = c.ex;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int er = (int)((ex >> (8 * q)) & 0xFFu);
+    const uint32_t eo = (ex >> (16 + 6 * q)) & 63u;
+    const int e0 = (int)(eo & 3u) - 1, e1 = (int)((eo >> 2) & 3u) - 1, e2 = (int)((eo >> 4) & 3u) - 1;
+    if (er != 0xFF && (o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= er) return false;
+  }
+  const uint32_t axes = c.axes;
+  if (!(axes & 512u)) {  // the ball may leave the array: check each coordinate
+    const int cx = (int)(c.idx % (uint32_t)d.nx);
+    const uint32_t t = c.idx / (uint32_t)d.nx;
+    const int cy = (int)(t % (uint32_t)d.ny), cz = (int)(t / (uint32_t)d.ny);
+    const int a0 = axes & 3, a1 = (axes >> 2) & 3, a2 = (axes >> 4) & 3;
+    const int v0 = (axes >> 6) & 1 ? -o0 : o0, v1 = (axes >> 7) & 1 ? -o1 : o1, v2 = (axes >> 8) & 1 ? -o2 : o2;
+    const int x = cx + (a0 == 0 ? v0 : 0) + (a1 == 0 ? v1 : 0) + (a2 == 0 ? v2 : 0);
+    const int y = cy + (a0 == 1 ? v0 : 0) + (a1 == 1 ? v1 : 0) + (a2 == 1 ? v2 : 0);
+    const int z = cz + (a0 == 2 ? v0 : 0) + (a1 == 2 ? v1 : 0) + (a2 == 2 ? v2 : 0);
+    if (x < 0 || x >= d.nx || y < 0 || y >= d.ny || z < 0 || z >= d.nz) return false;
+  }
+  i = c.idx + (uint32_t)(o0 * c.S[0] + o1 * c.S[1] + o2 * c.S[2]);  // modulo 2^32: the sum is in range
+  return true;
 }
 
 // Row-mode item `local` of a centre: the z offset and the group of 8 rows.
@@ -643,6 +694,123 @@ __device__ __forceinline__ void paint_row_item(const Centre& c, int local, const
   }
 }
 
+// Lane-parallel exclusive prefix sum of cnt over the warp; returns the
+// lane's start, the warp's total in *total.
+__device__ __forceinline__ int warp_starts(int cnt, int lane, int* total) {
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  *total = __shfl_sync(kFull, incl, 31);
+  return incl - cnt;
+}
+
+// Owner of work item k: the last lane whose start <= k.
+__device__ __forceinline__ int owner_lane(int start, int k) {
+  int j = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1) {
+    const int s = __shfl_sync(kFull, start, j + step);
+    if (s <= k) j += step;
+  }
+  return j;
+}
+
+// Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
+// crescent voxels, two per lane in flight. A warp takes kChunkGrab chunks
+// per counter update (one hot counter serialises its atomics).
+constexpr int kChunkGrab = 4;
+__device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
+                                                   size_t sy, size_t sz, bool touch,
+                                                   const uint32_t* __restrict__ dt2,
+                                                   const uint32_t* __restrict__ labels,
+                                                   uint32_t* __restrict__ lt2, WsHeader* __restrict__ hdr,
+                                                   uint32_t& ntab) {
+  __shared__ TabCentre cs[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t nchunks = (n + 31) / 32;
+  uint32_t ch = 0, grab_end = 0;
+  for (;;) {
+    if (ch == grab_end) {  // the next kChunkGrab chunks from the shared counter
+      if (lane == 0) ch = atomicAdd(&hdr->ctr_small, (uint32_t)kChunkGrab);
+      ch = __shfl_sync(kFull, ch, 0);
+      grab_end = ch + kChunkGrab;
+    }
+    if (ch >= nchunks) break;
+    const uint32_t i = ch++ * 32 + lane;
+    int cnt = 0;
+    if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, cs[w][lane]);
+    int total;
+    const int start = warp_starts(cnt, lane, &total);
+    if (i < n) cs[w][lane].start = start;
+    __syncwarp();
+    for (int kb = 0; kb < total; kb += 64) {
+      const int k0 = kb + lane, k1 = k0 + 32;
+      const int j0 = owner_lane(start, k0), j1 = owner_lane(start, k1);
+      const TabCentre& c0 = cs[w][j0];
+      const TabCentre& c1 = cs[w][j1];
+      const uint32_t p0 = k0 < total ? g_cres_vox[c0.vstart + (uint32_t)(k0 - c0.start)] : 0u;
+      const uint32_t p1 = k1 < total ? g_cres_vox[c1.vstart + (uint32_t)(k1 - c1.start)] : 0u;
+      uint32_t i0 = 0, i1 = 0;
+      bool w0 = k0 < total && tab_voxel_index(c0, p0, d, i0);
+      bool w1 = k1 < total && tab_voxel_index(c1, p1, d, i1);
+      // inside the ball only the sphere |y|^2 == r^2 can be background
+      const uint32_t b0 = w0 && (p0 >> 24) ? dt2[i0] : 1u;
+      const uint32_t b1 = w1 && (p1 >> 24) ? dt2[i1] : 1u;
+      if (touch) {
+        w0 = w0 && labels[i0] == c0.label;
+        w1 = w1 && labels[i1] == c1.label;
+      }
+      if (w0 && b0) {
+        atomicMax(lt2 + i0, c0.r2);
+        ++ntab;
+      }
+      if (w1 && b1) {
+        atomicMax(lt2 + i1, c1.r2);
+        ++ntab;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Phase 2 in 2D: chunks of 32 centres; the lanes share the chunk's row
+// segments.
+__device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
+                                                 size_t sy, size_t sz, bool touch,
+                                                 const uint32_t* __restrict__ dt2,
+                                                 const uint32_t* __restrict__ labels,
+                                                 uint32_t* __restrict__ lt2, WsHeader* __restrict__ hdr,
+                                                 uint32_t& nupd) {
+  __shared__ Centre cs[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t nchunks = (n + 31) / 32;
+  for (;;) {
+    uint32_t ch = 0;
+    if (lane == 0) ch = atomicAdd(&hdr->ctr_small, 1u);
+    ch = __shfl_sync(kFull, ch, 0);
+    if (ch >= nchunks) break;
+    const uint32_t i = ch * 32 + lane;
+    int cnt = 0;
+    if (i < n) cnt = make_centre<2>(surv[i], d, sy, sz, touch, dt2, labels, cs[w][lane]);
+    int total;
+    const int start = warp_starts(cnt, lane, &total);
+    if (i < n) cs[w][lane].start = start;
+    __syncwarp();
+    for (int kb = 0; kb < total; kb += 32) {
+      const int k = kb + lane;
+      const int j = owner_lane(start, k);
+      if (k < total) {
+        const Centre& c = cs[w][j];
+        paint_row_item<2>(c, k - c.start, d, sy, sz, touch, dt2, labels, lt2, nupd);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Two phases, each fed by a global work counter.
 // 1. (3D) Row-mode centres from the back of the list, one per warp: the
 //    lanes share its (2R+1) * ceil((2R+1)/8) row segments. These are the
@@ -656,8 +824,7 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
                                                        WsHeader* __restrict__ hdr) {
-  __shared__ Centre cs[8][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const uint32_t n = *(volatile uint32_t*)&hdr->n_surv;
   const uint32_t nbig = *(volatile uint32_t*)&hdr->n_big;
   const bool touch = *(volatile uint32_t*)&hdr->touch != 0;
@@ -670,50 +837,12 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
       b = __shfl_sync(kFull, b, 0);
       if (b >= nbig) break;
       Centre c;
-      const int items = make_centre<NDIM>(surv[(size_t)d.n - 1 - b], false, d, sy, sz, touch, dt2, labels, c);
-      for (int k = lane; k < items; k += 32) paint_row_item<NDIM>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
+      const int items = make_centre<3>(surv[(size_t)d.n - 1 - b], d, sy, sz, touch, dt2, labels, c);
+      for (int k = lane; k < items; k += 32) paint_row_item<3>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
     }
-  }
-  const uint32_t nchunks = (n + 31) / 32;
-  for (;;) {
-    uint32_t ch = 0;
-    if (lane == 0) ch = atomicAdd(&hdr->ctr_small, 1u);
-    ch = __shfl_sync(kFull, ch, 0);
-    if (ch >= nchunks) break;
-    const uint32_t i = ch * 32 + lane;
-    int cnt = 0;
-    if (i < n) {
-      Centre c;
-      cnt = make_centre<NDIM>(surv[i], true, d, sy, sz, touch, dt2, labels, c);
-      cs[w][lane] = c;
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int start = incl - cnt;
-    if (i < n) cs[w][lane].start = start;
-    const int total = __shfl_sync(kFull, incl, 31);
-    __syncwarp();
-    for (int kb = 0; kb < total; kb += 32) {
-      const int k = kb + lane;
-      int j = 0;  // owner: the last lane whose start <= k
-#pragma unroll
-      for (int step = 16; step; step >>= 1) {
-        const int s = __shfl_sync(kFull, start, j + step);
-        if (s <= k) j += step;
-      }
-      if (k >= total) continue;
-      const Centre& c = cs[w][j];
-      const int local = k - c.start;
-      if (c.mode)
-        paint_table_voxel(c, (uint32_t)local, d, touch, dt2, labels, lt2, ntab);
-      else
-        paint_row_item<NDIM>(c, local, d, sy, sz, touch, dt2, labels, lt2, nupd);
-    }
-    __syncwarp();
+    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
+  } else {
+    paint_row_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, nupd);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
