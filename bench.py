@@ -373,7 +373,7 @@ def main():
         lt.lt_measure(m, l, n_labels, dt2, lt2, S, R, ws=ws)
     lt.lt_workspace_status(ws)
     counters = lt.lt_workspace_counters(ws)
-    n_surv = counters["table_centres"] + counters["row_centres"]
+    n_surv = counters["chunk_centres"] + counters["warp_centres"]
 
     clocks = ClockSampler(local)
     clocks.start()

@@ -305,13 +305,14 @@ int lt_trace_summary(lt_trace_entry* out, int max_entries);
 lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream);
 
 /* Work counters of the last lt_local_thickness (or lt_measure) that used
- * `ws`, after waiting for `stream`: centres kept by the containment test and
- * painted from crescent tables (table_centres) or row by row (row_centres),
- * and the LT2 updates (32-bit atomic max) the painting issued, in total and
- * from crescent tables. */
+ * `ws`, after waiting for `stream`: centres kept by the containment test,
+ * painted by warps sharing chunks of 32 centres (chunk_centres) or by one
+ * warp each (warp_centres: big crescents and balls painted row by row), and
+ * the LT2 updates (32-bit atomic max) the painting issued, in total and from
+ * crescent tables. */
 typedef struct lt_lt_counters {
-  uint32_t table_centres;
-  uint32_t row_centres;
+  uint32_t chunk_centres;
+  uint32_t warp_centres;
   uint64_t updates;
   uint64_t table_updates;
 } lt_lt_counters;

@@ -75,7 +75,7 @@ class LTError(RuntimeError):
 
 
 class LTCounters(ctypes.Structure):
-    _fields_ = [("table_centres", ctypes.c_uint32), ("row_centres", ctypes.c_uint32),
+    _fields_ = [("chunk_centres", ctypes.c_uint32), ("warp_centres", ctypes.c_uint32),
                 ("updates", ctypes.c_uint64), ("table_updates", ctypes.c_uint64)]
 
 
@@ -224,12 +224,13 @@ def lt_workspace_status(ws, stream=None):
 
 def lt_workspace_counters(ws, stream=None):
     """Work counters of the last local-thickness run on `ws`: dict with
-    table_centres, row_centres, updates (LT2 atomic-max updates) and
-    table_updates (those from crescent tables)."""
+    chunk_centres, warp_centres (kept centres painted in shared chunks or
+    one warp each), updates (LT2 atomic-max updates) and table_updates
+    (those from crescent tables)."""
     c = LTCounters()
     _check(lib.lt_workspace_counters(_ptr(ws), ws.numel(), _stream(stream), ctypes.byref(c)),
            "workspace counters")
-    return {"table_centres": c.table_centres, "row_centres": c.row_centres, "updates": c.updates,
+    return {"chunk_centres": c.chunk_centres, "warp_centres": c.warp_centres, "updates": c.updates,
             "table_updates": c.table_updates}
 
 

@@ -298,8 +298,8 @@ lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, l
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
   WsHeader h;
   if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LT_ERR_CUDA;
-  out->table_centres = h.n_surv;
-  out->row_centres = h.n_big;
+  out->chunk_centres = h.n_surv;
+  out->warp_centres = h.n_big;
   out->updates = h.n_updates;
   out->table_updates = h.n_table_updates;
   return LT_OK;

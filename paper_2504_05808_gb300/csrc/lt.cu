@@ -65,6 +65,8 @@ constexpr int kCresT = 144;           // crescent tables cover r^2 <= 144
 constexpr int kCresMaxCombos = 12288;
 constexpr int kCresMaxVoxels = 2304 * 1024;  // both orderings (about 2.16 M voxels)
 constexpr uint32_t kNoDominant = 31u;
+constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a crescent table
+constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
 constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
@@ -213,16 +215,18 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // labelled foreground voxels are compacted to the front of the CTA so that
 // the 26-neighbour (8 in 2D) test runs on full warps; every neighbour is
 // evaluated without early exit. Kept centres collect in one shared buffer
-// (table list from its front, row list from its back) and leave with one
-// global atomic per list every kRidgeFlush planes: centres painted from
-// crescent tables (3D, r^2 <= kCresT, with a dominant neighbour; every 2D
-// centre) go to the front of `surv`, the others (painted row by row) to the
-// back.
+// (front list from its front, back list from its back) and leave with one
+// global atomic per list every kRidgeFlush planes. The front of `surv` gets
+// the centres painted in shared chunks: 3D centres with r^2 <= kCresT, a
+// dominant neighbour and a crescent of at most kChunkCres voxels, and every
+// 2D centre. The back gets those a warp paints alone: bigger crescents and
+// the centres painted row by row.
 // Records (uint4). Offset codes: (dz+1)*9 + (dy+1)*3 + (dx+1), 31 for none.
 //   Table centres (3D): x = linear index; y = first crescent voxel | crescent
 //   size << 22; z = r^2 | dominant code << 8 | codes of up to two more
 //   higher-ranked same-label neighbours << 13 (5 bits each) | ball inside
-//   the array << 23; w = those two neighbours' r^2 (8 bits each, 0xFF none).
+//   the array << 23 | kTableRecord; w = those two neighbours' r^2 (8 bits
+//   each, 0xFF none).
 //   Painting needs no other lookup.
 //   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
 //   z = the two extra codes.
@@ -448,12 +452,14 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           const int R = (int)isqrt24(r2);
           const int x = x0 + tx, y = y0 + ty;
           const uint32_t inside = x >= R && x + R < d.nx && y >= R && y + R < d.ny && z >= R && z + R < d.nz;
-          rec = make_uint4(v, vstart | (best << 22), r2 | (code << 8) | (extra << 13) | (inside << 23), er);
+          rec = make_uint4(v, vstart | (best << 22),
+                           r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord, er);
         } else {
           rec = make_uint4(v, r2 | (code << 25), extra, 0u);
         }
-        keepA = tab;
-        keepB = !tab;
+        // small crescents are shared out in chunks; a big one takes a warp
+        keepA = tab && (NDIM == 2 || best <= (uint32_t)kChunkCres);
+        keepB = !keepA;
       }
     }
     // at most 256 * kRidgeFlush records between flushes: list A grows from
@@ -722,6 +728,7 @@ __device__ __forceinline__ int owner_lane(int start, int k) {
 // crescent voxels, two per lane in flight. A warp takes kChunkGrab chunks
 // per counter update (one hot counter serialises its atomics).
 constexpr int kChunkGrab = 4;
+constexpr int kBigGrab = 2;  // phase 1 centres per counter update
 __device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
                                                    size_t sy, size_t sz, bool touch,
                                                    const uint32_t* __restrict__ dt2,
@@ -812,9 +819,10 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
 }
 
 // Two phases, each fed by a global work counter.
-// 1. (3D) Row-mode centres from the back of the list, one per warp: the
-//    lanes share its (2R+1) * ceil((2R+1)/8) row segments. These are the
-//    biggest balls, so they go first.
+// 1. (3D) Centres from the back of the list, one per warp: the lanes share
+//    its crescent voxels (big table crescents) or its (2R+1) * ceil((2R+1)/8)
+//    row segments (row mode). These are the biggest pieces of work, so they
+//    go first.
 // 2. Chunks of 32 centres from the front of the list: the 32 lanes share the
 //    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
 //    and small crescents balance.
@@ -831,14 +839,32 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   uint32_t nupd = 0, ntab = 0;  // updates this thread issued: row by row, from tables
   if (NDIM == 3) {
+    uint32_t b = 0, grab_end = 0;
     for (;;) {
-      uint32_t b = 0;
-      if (lane == 0) b = atomicAdd(&hdr->ctr_big, 1u);
-      b = __shfl_sync(kFull, b, 0);
+      if (b == grab_end) {  // the next kBigGrab centres from the shared counter
+        if (lane == 0) b = atomicAdd(&hdr->ctr_big, (uint32_t)kBigGrab);
+        b = __shfl_sync(kFull, b, 0);
+        grab_end = b + kBigGrab;
+      }
       if (b >= nbig) break;
-      Centre c;
-      const int items = make_centre<3>(surv[(size_t)d.n - 1 - b], d, sy, sz, touch, dt2, labels, c);
-      for (int k = lane; k < items; k += 32) paint_row_item<3>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
+      const uint4 rec = surv[(size_t)d.n - 1 - b++];
+      if (rec.z & kTableRecord) {
+        TabCentre c;
+        const int items = make_tab_centre(rec, sy, sz, touch, labels, c);
+        for (int k = lane; k < items; k += 32) {
+          const uint32_t p = g_cres_vox[c.vstart + (uint32_t)k];
+          uint32_t i = 0;
+          if (!tab_voxel_index(c, p, d, i)) continue;
+          if ((p >> 24) && dt2[i] == 0) continue;  // only the sphere can be background
+          if (touch && labels[i] != c.label) continue;
+          atomicMax(lt2 + i, c.r2);
+          ++ntab;
+        }
+      } else {
+        Centre c;
+        const int items = make_centre<3>(rec, d, sy, sz, touch, dt2, labels, c);
+        for (int k = lane; k < items; k += 32) paint_row_item<3>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
+      }
     }
     paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
   } else {

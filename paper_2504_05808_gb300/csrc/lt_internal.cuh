@@ -22,8 +22,8 @@ struct Dims {
 struct WsHeader {
   uint32_t error;   // bit set of ERR_* found on the device
   uint32_t touch;   // nonzero: two face-adjacent foreground voxels differ in label
-  uint32_t n_surv;  // kept centres painted from crescent tables (list from the front)
-  uint32_t n_big;   // kept centres painted row by row (list from the back)
+  uint32_t n_surv;  // kept centres painted in shared chunks (list from the front)
+  uint32_t n_big;   // kept centres painted by one warp each (list from the back)
   uint32_t ctr_small, ctr_big;  // work counters of the paint kernel
   unsigned long long n_updates;        // LT2 updates (atomic max) the paint kernel issued
   unsigned long long n_table_updates;  // of which from crescent tables
