@@ -100,9 +100,10 @@ uint32_t lt_version(void);
  * parabolas f(q) + (p - q)^2 along y and (3D) along z, with the padding
  * layer entering as two zero-height parabolas at -1 and n. All arithmetic is
  * exact integer arithmetic, so the result is bit-exact.
- * Workspace: lt_edt_workspace_size bytes (0 for every axis length up to
- * 2048, where the strided passes run fully in shared memory; otherwise one
- * uint32 per voxel). `ws` may be NULL when the size is 0. */
+ * Workspace: lt_edt_workspace_size bytes: 2 bytes per voxel (the row pass
+ * leaves 16-bit distances there for the y pass), plus 4 bytes per voxel in
+ * 3D when nz > 2048 (columns longer than 2048 do not fit in shared memory;
+ * that z pass goes out of place). */
 size_t lt_edt_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
 lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64_t ny, int64_t nz,
                  void* ws, size_t ws_bytes, void* stream);
@@ -161,7 +162,7 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
  * the same kernels volume after volume on `stream`, the per-volume baseline.
  * lt_batch_status waits for `stream` and returns the first device-detected
  * error of any volume. lt_batch_autotune times candidate settings (branch
- * count, EDT column-tile width, ridge z-chunk, paint grid) on the batch
+ * count, EDT column-tile widths, ridge z-chunk, paint grid) on the batch
  * itself, one setting at a time from the defaults, keeps the fastest and
  * rebuilds the graph; results are cached in the JSON file `cache_path`
  * (NULL: no cache) under the GPU name and the batch's shape class, and a
@@ -187,8 +188,9 @@ lt_status lt_batch_run(lt_batch* batch, void* stream);
 lt_status lt_batch_run_eager(lt_batch* batch, void* stream);
 lt_status lt_batch_status(lt_batch* batch, void* stream);
 lt_status lt_batch_autotune(lt_batch* batch, void* stream, const char* cache_path);
-/* current settings: branches, EDT tile width, ridge z-chunk, paint CTAs per SM */
-lt_status lt_batch_settings(const lt_batch* batch, int32_t out[4]);
+/* current settings: branches, EDT y and z column-tile widths, ridge z-chunk,
+ * paint CTAs per SM */
+lt_status lt_batch_settings(const lt_batch* batch, int32_t out[5]);
 void lt_batch_destroy(lt_batch* batch);
 
 /* ------------------------------------------------ learned sphericity --

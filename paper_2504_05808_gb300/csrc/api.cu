@@ -110,7 +110,7 @@ cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
   void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
-  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(body), s, tu);
+  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, body, s, tu);
   if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s, tu);
   if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
   return e;
@@ -153,7 +153,7 @@ lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64
   if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(dt2)) != LT_OK) return st;
   const size_t need = edt_workspace_bytes(d);
   if ((st = check_ws(ws, ws_bytes, need)) != LT_OK) return st;
-  return cuda_status(edt_launch(mask, dt2, d, reinterpret_cast<uint32_t*>(ws), as_stream(stream)));
+  return cuda_status(edt_launch(mask, dt2, d, ws, as_stream(stream)));
 }
 
 size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz) {

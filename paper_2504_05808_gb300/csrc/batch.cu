@@ -129,10 +129,11 @@ std::string shape_class(const lt_batch* b) {
   return buf;
 }
 
-// ---- minimal JSON cache: {"key": {"branches": 4, "edt_tx": 32, ...}, ...}
+// ---- minimal JSON cache: {"key": {"branches": 4, "edt_tx_y": 8, ...}, ...}
+constexpr int kSettings = 5;  // branches, EDT y and z tile widths, ridge z-chunk, paint CTAs/SM
 struct CacheEntry {
   std::string key;
-  int v[4];
+  int v[kSettings];
   double ms;
 };
 
@@ -146,7 +147,8 @@ std::vector<CacheEntry> read_cache(const char* path) {
   size_t k;
   while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
   std::fclose(f);
-  static const char* names[4] = {"\"branches\"", "\"edt_tx\"", "\"ridge_z\"", "\"paint_bpsm\""};
+  static const char* names[kSettings] = {"\"branches\"", "\"edt_tx_y\"", "\"edt_tx_z\"", "\"ridge_z\"",
+                                         "\"paint_bpsm\""};
   size_t pos = 0;
   while (true) {
     const size_t q0 = text.find('"', pos);
@@ -159,7 +161,7 @@ std::vector<CacheEntry> read_cache(const char* path) {
     e.key = text.substr(q0 + 1, q1 - q0 - 1);
     const std::string body = text.substr(ob, cb - ob);
     bool ok = true;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kSettings; ++i) {
       const size_t p = body.find(names[i]);
       if (p == std::string::npos) {
         ok = false;
@@ -183,26 +185,30 @@ bool write_cache(const char* path, const std::vector<CacheEntry>& entries) {
   std::fprintf(f, "{\n");
   for (size_t i = 0; i < entries.size(); ++i) {
     const CacheEntry& e = entries[i];
-    std::fprintf(f, "  \"%s\": {\"branches\": %d, \"edt_tx\": %d, \"ridge_z\": %d, \"paint_bpsm\": %d, \"ms\": %.4f}%s\n",
-                 e.key.c_str(), e.v[0], e.v[1], e.v[2], e.v[3], e.ms, i + 1 < entries.size() ? "," : "");
+    std::fprintf(f,
+                 "  \"%s\": {\"branches\": %d, \"edt_tx_y\": %d, \"edt_tx_z\": %d, \"ridge_z\": %d, "
+                 "\"paint_bpsm\": %d, \"ms\": %.4f}%s\n",
+                 e.key.c_str(), e.v[0], e.v[1], e.v[2], e.v[3], e.v[4], e.ms, i + 1 < entries.size() ? "," : "");
   }
   std::fprintf(f, "}\n");
   std::fclose(f);
   return std::rename(tmp.c_str(), path) == 0;
 }
 
-void apply(lt_batch* b, const int v[4]) {
+void apply(lt_batch* b, const int v[kSettings]) {
   b->branches = std::max(1, std::min(kMaxBranches, v[0]));
-  b->tu.edt_tx_small = v[1] == 16 ? 16 : 32;
-  b->tu.ridge_z = v[2] == 8 || v[2] == 32 ? v[2] : 16;
-  b->tu.paint_blocks_per_sm = std::max(1, std::min(32, v[3]));
+  b->tu.edt_tx_y = v[1] == 8 || v[1] == 16 ? v[1] : 32;
+  b->tu.edt_tx_z = v[2] == 8 || v[2] == 16 ? v[2] : 32;
+  b->tu.ridge_z = v[3] == 8 || v[3] == 32 ? v[3] : 16;
+  b->tu.paint_blocks_per_sm = std::max(1, std::min(32, v[4]));
 }
 
-void current(const lt_batch* b, int v[4]) {
+void current(const lt_batch* b, int v[kSettings]) {
   v[0] = b->branches;
-  v[1] = b->tu.edt_tx_small;
-  v[2] = b->tu.ridge_z;
-  v[3] = b->tu.paint_blocks_per_sm;
+  v[1] = b->tu.edt_tx_y;
+  v[2] = b->tu.edt_tx_z;
+  v[3] = b->tu.ridge_z;
+  v[4] = b->tu.paint_blocks_per_sm;
 }
 
 // mean ms of `reps` graph launches (after one warm-up launch)
@@ -318,15 +324,15 @@ lt_status lt_batch_autotune(lt_batch* b, void* stream, const char* cache_path) {
       apply(b, e.v);
       return record(b);
     }
-  int best[4];
+  int best[kSettings];
   current(b, best);
   double best_ms = 0.0;
   lt_status st = time_graph(b, s, 3, &best_ms);
   if (st != LT_OK) return st;
-  const std::vector<int> cand[4] = {{1, 2, 4, 8, 16}, {32, 16}, {8, 16, 32}, {4, 6, 8, 12}};
-  for (int axis = 0; axis < 4; ++axis) {
+  const std::vector<int> cand[kSettings] = {{1, 2, 4, 8, 16}, {32, 16, 8}, {32, 16, 8}, {8, 16, 32}, {4, 6, 8, 12}};
+  for (int axis = 0; axis < kSettings; ++axis) {
     for (int c : cand[axis]) {
-      int v[4];
+      int v[kSettings];
       std::memcpy(v, best, sizeof(v));
       if (v[axis] == c) continue;
       v[axis] = c;
@@ -353,11 +359,11 @@ lt_status lt_batch_autotune(lt_batch* b, void* stream, const char* cache_path) {
   return LT_OK;
 }
 
-lt_status lt_batch_settings(const lt_batch* b, int32_t out[4]) {
+lt_status lt_batch_settings(const lt_batch* b, int32_t out[5]) {
   if (!b || !out) return LT_ERR_INVALID_ARG;
-  int v[4];
+  int v[kSettings];
   current(b, v);
-  for (int i = 0; i < 4; ++i) out[i] = v[i];
+  for (int i = 0; i < kSettings; ++i) out[i] = v[i];
   return LT_OK;
 }
 

@@ -3,7 +3,8 @@
 // Separable form of DT2(p) = min over background b of |p - b|^2 with the
 // array padded by one background layer:
 //   pass x:  g(p)  = distance along the row to the nearest background voxel
-//                    (positions -1 and nx count as background); out = g^2.
+//                    (positions -1 and nx count as background); written as
+//                    16-bit g (<= 8193) to scratch, squared on loading.
 //   pass y:  f(p)  = min_q g^2(x, q, z) + (y - q)^2, plus the two padding
 //                    rows at y = -1 and y = ny (height 0).
 //   pass z:  same along z on f, giving DT2.
@@ -44,16 +45,16 @@ __device__ __forceinline__ uint32_t zero_bits(const uint8_t* __restrict__ row, i
   return bits;
 }
 
-// One warp per row. Output: g^2 per voxel (0 on background).
+// One warp per row. Output: g per voxel (0 on background), 16 bits.
 template <bool VEC>
 __global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict__ mask,
-                                                       uint32_t* __restrict__ out, int nx,
+                                                       uint16_t* __restrict__ out, int nx,
                                                        uint32_t nrows) {
   const int lane = threadIdx.x & 31;
   const uint32_t row = blockIdx.x * 8u + (threadIdx.x >> 5);
   if (row >= nrows) return;  // uniform per warp
   const uint8_t* mrow = mask + (size_t)row * nx;
-  uint32_t* orow = out + (size_t)row * nx;
+  uint16_t* orow = out + (size_t)row * nx;
   const int nseg = (nx + kSeg - 1) / kSeg;  // <= 16
 
   // First background position of each segment, held by lane == segment.
@@ -110,30 +111,32 @@ __global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict
       if ((z >> j) & 1u) L = x0 + j;
       lpos[j] = L;
     }
-    uint32_t g2[16];
+    uint32_t g[16];
     int R = right;
 #pragma unroll
     for (int j = 15; j >= 0; --j) {
       if ((z >> j) & 1u) R = x0 + j;
       const int x = x0 + j;
-      const int g = min(x - lpos[j], R - x);
-      g2[j] = (uint32_t)(g * g);
+      g[j] = (uint32_t)min(x - lpos[j], R - x);
     }
     if (VEC && x0 + 16 <= nx) {
       uint4* o4 = reinterpret_cast<uint4*>(orow + x0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) o4[k] = make_uint4(g2[4 * k], g2[4 * k + 1], g2[4 * k + 2], g2[4 * k + 3]);
+      for (int k = 0; k < 2; ++k)
+        o4[k] = make_uint4(g[8 * k] | (g[8 * k + 1] << 16), g[8 * k + 2] | (g[8 * k + 3] << 16),
+                           g[8 * k + 4] | (g[8 * k + 5] << 16), g[8 * k + 6] | (g[8 * k + 7] << 16));
     } else {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (x0 + j < nx) orow[x0 + j] = g2[j];
+        if (x0 + j < nx) orow[x0 + j] = (uint16_t)g[j];
     }
   }
 }
 
 // Lower envelope at p. best starts at min(f(p), (p+1)^2, (L-p)^2), the last
 // two being the padding parabolas; the scan only visits k with k^2 < best,
-// hence k <= p and p + k < L: no bounds checks are needed.
+// hence k <= p and p + k < L: no bounds checks are needed. Two distances per
+// step, the second only when its k^2 is still below best.
 __device__ __forceinline__ uint32_t envelope_at(const uint32_t* __restrict__ col, int stride, int p,
                                                 int L) {
   uint32_t best = col[p * stride];
@@ -145,141 +148,183 @@ __device__ __forceinline__ uint32_t envelope_at(const uint32_t* __restrict__ col
   const uint32_t* hi = lo;
   uint32_t k2 = 1, dk = 3;  // k^2 and (k+1)^2 - k^2
   while (k2 < best) {
-    lo -= stride;
-    hi += stride;
-    best = min(best, min(*lo, *hi) + k2);
-    k2 += dk;
-    dk += 2;
+    best = min(best, min(lo[-stride], hi[stride]) + k2);
+    const uint32_t k2b = k2 + dk;
+    if (k2b >= best) break;
+    best = min(best, min(lo[-2 * stride], hi[2 * stride]) + k2b);
+    lo -= 2 * stride;
+    hi += 2 * stride;
+    k2 = k2b + dk + 2;
+    dk += 4;
   }
   return best;
 }
 
+// Loads four consecutive elements of a column tile row as uint32 values:
+// 16-bit row-pass distances are squared, 32-bit values copied.
+__device__ __forceinline__ uint4 load4(const uint16_t* src, bool vec, int n) {
+  uint32_t v[4];
+  if (vec) {
+    const uint2 q = *reinterpret_cast<const uint2*>(src);
+    v[0] = q.x & 0xFFFFu; v[1] = q.x >> 16; v[2] = q.y & 0xFFFFu; v[3] = q.y >> 16;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = j < n ? src[j] : 0u;
+  }
+  return make_uint4(v[0] * v[0], v[1] * v[1], v[2] * v[2], v[3] * v[3]);
+}
+__device__ __forceinline__ uint4 load4(const uint32_t* src, bool vec, int n) {
+  if (vec) return *reinterpret_cast<const uint4*>(src);
+  return make_uint4(0 < n ? src[0] : 0u, 1 < n ? src[1] : 0u, 2 < n ? src[2] : 0u, 3 < n ? src[3] : 0u);
+}
+__device__ __forceinline__ uint32_t load1(const uint16_t* src) { return (uint32_t)*src * (uint32_t)*src; }
+__device__ __forceinline__ uint32_t load1(const uint32_t* src) { return *src; }
+
 // Column pass in shared memory. Tile: TX adjacent columns x the whole axis
 // (length L, stride sp between elements); blockIdx.y picks the other
-// coordinate (stride so). In place.
-template <int TX>
-__global__ void __launch_bounds__(256) edt_cols_kernel(uint32_t* __restrict__ data, int L, size_t sp,
+// coordinate (stride so). `in` and `out` have the same layout and may be the
+// same array (the tile is read completely before anything is written).
+template <int TX, typename In>
+__global__ void __launch_bounds__(256) edt_cols_kernel(const In* in, uint32_t* out, int L, size_t sp,
                                                        int nx, size_t so, int vec) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* tile = reinterpret_cast<uint32_t*>(smem_raw);
+  constexpr int Q = TX / 4;           // 4-element pieces per tile row
+  constexpr int kRows = 256 / Q;      // tile rows loaded per sweep of the CTA
+  constexpr int kOutRows = 256 / TX;  // tile rows computed per sweep
   const int x0 = blockIdx.x * TX;
-  uint32_t* base = data + (size_t)blockIdx.y * so + x0;
+  const size_t off = (size_t)blockIdx.y * so + x0;
   const int ncol = min(TX, nx - x0);
-  constexpr int Q = TX / 4;
-  for (int i = threadIdx.x; i < L * Q; i += blockDim.x) {
-    const int p = i / Q, qd = i % Q;
-    const uint32_t* src = base + (size_t)p * sp + qd * 4;
-    uint4 v;
-    if (vec && qd * 4 + 4 <= ncol) {
-      v = *reinterpret_cast<const uint4*>(src);
-    } else {
-      v.x = qd * 4 + 0 < ncol ? src[0] : 0u;
-      v.y = qd * 4 + 1 < ncol ? src[1] : 0u;
-      v.z = qd * 4 + 2 < ncol ? src[2] : 0u;
-      v.w = qd * 4 + 3 < ncol ? src[3] : 0u;
+  {
+    const int qd = threadIdx.x % Q;
+    const bool v = vec && qd * 4 + 4 <= ncol;
+    const In* src = in + off + (size_t)(threadIdx.x / Q) * sp + qd * 4;
+    uint32_t* dst = tile + (threadIdx.x / Q) * TX + qd * 4;
+    for (int p = threadIdx.x / Q; p < L; p += kRows) {
+      *reinterpret_cast<uint4*>(dst) = load4(src, v, ncol - qd * 4);
+      src += kRows * sp;
+      dst += kRows * TX;
     }
-    *reinterpret_cast<uint4*>(tile + p * TX + qd * 4) = v;
   }
   __syncthreads();
   const int c = threadIdx.x % TX;
-  const int nrg = blockDim.x / TX;
   if (c < ncol) {
-    for (int p = threadIdx.x / TX; p < L; p += nrg) base[(size_t)p * sp + c] = envelope_at(tile + c, TX, p, L);
+    uint32_t* o = out + off + (size_t)(threadIdx.x / TX) * sp + c;
+    for (int p = threadIdx.x / TX; p < L; p += kOutRows) {
+      *o = envelope_at(tile + c, TX, p, L);
+      o += kOutRows * sp;
+    }
   }
 }
 
 // Column pass reading `in` and writing `out` directly (axes longer than the
-// shared-memory tile allows).
-__global__ void __launch_bounds__(256) edt_cols_global_kernel(const uint32_t* __restrict__ in,
+// shared-memory tile allows); `in` and `out` must differ.
+template <typename In>
+__global__ void __launch_bounds__(256) edt_cols_global_kernel(const In* __restrict__ in,
                                                               uint32_t* __restrict__ out, int L,
                                                               size_t sp, int nx, size_t so,
                                                               int rows_per_block) {
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   if (c >= nx) return;
   const size_t off = (size_t)blockIdx.y * so + c;
-  const uint32_t* col = in + off;
+  const In* col = in + off;
   const int p0 = blockIdx.z * rows_per_block;
   const int p1 = min(L, p0 + rows_per_block);
   for (int p = p0 + (threadIdx.x >> 5); p < p1; p += blockDim.x >> 5) {
-    uint32_t best = col[(size_t)p * sp];
+    uint32_t best = load1(col + (size_t)p * sp);
     if (best) {
       const uint32_t b1 = (uint32_t)(p + 1) * (uint32_t)(p + 1);
       const uint32_t b2 = (uint32_t)(L - p) * (uint32_t)(L - p);
       best = min(best, min(b1, b2));
       for (uint32_t k = 1; k * k < best; ++k) {
-        if ((uint32_t)p >= k) best = min(best, col[(size_t)(p - (int)k) * sp] + k * k);
-        if (p + (int)k < L) best = min(best, col[(size_t)(p + (int)k) * sp] + k * k);
+        if ((uint32_t)p >= k) best = min(best, load1(col + (size_t)(p - (int)k) * sp) + k * k);
+        if (p + (int)k < L) best = min(best, load1(col + (size_t)(p + (int)k) * sp) + k * k);
       }
     }
     out[off + (size_t)p * sp] = best;
   }
 }
 
-template <int TX>
-cudaError_t launch_cols(const char* name, uint32_t* data, int L, size_t sp, int nx, size_t so,
+template <int TX, typename In>
+cudaError_t launch_cols(const char* name, const In* in, uint32_t* out, int L, size_t sp, int nx, size_t so,
                         int nother, bool vec, cudaStream_t s) {
   const int smem = L * TX * 4;
-  cudaError_t e = allow_smem((const void*)edt_cols_kernel<TX>, smem);
+  cudaError_t e = allow_smem((const void*)edt_cols_kernel<TX, In>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nx + TX - 1) / TX, nother);
   {
     TraceScope t(name, s);
-    edt_cols_kernel<TX><<<grid, 256, smem, s>>>(data, L, sp, nx, so, vec ? 1 : 0);
+    edt_cols_kernel<TX, In><<<grid, 256, smem, s>>>(in, out, L, sp, nx, so, vec ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
-cudaError_t col_pass(const char* name, uint32_t* data, int L, size_t sp, int nx, size_t so, int nother,
-                     uint32_t* tmp, size_t n, cudaStream_t s, int tx_small) {
+// One strided pass from `in` into `out` (the same array is allowed except for
+// axes over 2048, which go through `tmp`, n uint32 values).
+template <typename In>
+cudaError_t col_pass(const char* name, const In* in, uint32_t* out, int L, size_t sp, int nx, size_t so,
+                     int nother, uint32_t* tmp, size_t n, cudaStream_t s, int tx_small) {
   const bool vec = (nx % 4) == 0;
-  if (L <= 512 && tx_small == 16) return launch_cols<16>(name, data, L, sp, nx, so, nother, vec, s);
-  if (L <= 512) return launch_cols<32>(name, data, L, sp, nx, so, nother, vec, s);
-  if (L <= 1024) return launch_cols<16>(name, data, L, sp, nx, so, nother, vec, s);
-  if (L <= 2048) return launch_cols<8>(name, data, L, sp, nx, so, nother, vec, s);
+  if (L <= 512 && tx_small == 8) return launch_cols<8>(name, in, out, L, sp, nx, so, nother, vec, s);
+  if (L <= 512 && tx_small == 16) return launch_cols<16>(name, in, out, L, sp, nx, so, nother, vec, s);
+  if (L <= 512) return launch_cols<32>(name, in, out, L, sp, nx, so, nother, vec, s);
+  if (L <= 1024) return launch_cols<16>(name, in, out, L, sp, nx, so, nother, vec, s);
+  if (L <= 2048) return launch_cols<8>(name, in, out, L, sp, nx, so, nother, vec, s);
+  const bool inplace = (const void*)in == (const void*)out;
   const int rpb = 64;
   dim3 grid((nx + 31) / 32, nother, (L + rpb - 1) / rpb);
   {
     TraceScope t(name, s);
-    edt_cols_global_kernel<<<grid, 256, 0, s>>>(data, tmp, L, sp, nx, so, rpb);
+    edt_cols_global_kernel<In><<<grid, 256, 0, s>>>(in, inplace ? tmp : out, L, sp, nx, so, rpb);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyAsync(data, tmp, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess || !inplace) return e;
+  return cudaMemcpyAsync(out, tmp, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace
 
 cudaError_t edt_prepare_device() {
-  cudaError_t e = allow_smem((const void*)edt_cols_kernel<32>, 64 * 1024);
-  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<16>, 64 * 1024);
-  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<8>, 64 * 1024);
+  cudaError_t e = cudaSuccess;
+  e = allow_smem((const void*)edt_cols_kernel<32, uint16_t>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<16, uint16_t>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<8, uint16_t>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<32, uint32_t>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<16, uint32_t>, 64 * 1024);
+  if (e == cudaSuccess) e = allow_smem((const void*)edt_cols_kernel<8, uint32_t>, 64 * 1024);
   return e;
 }
 
+// Scratch: the row pass's 16-bit distances, then (z axes over 2048) one
+// uint32 per voxel for the out-of-place z pass.
 size_t edt_workspace_bytes(const Dims& d) {
-  const int longest = d.ndim == 3 ? (d.ny > d.nz ? d.ny : d.nz) : d.ny;
-  return longest > 2048 ? (size_t)d.n * sizeof(uint32_t) : 0;
+  const size_t g = align_up((size_t)d.n * sizeof(uint16_t));
+  return d.ndim == 3 && d.nz > 2048 ? g + (size_t)d.n * sizeof(uint32_t) : g;
 }
 
-cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
-                       cudaStream_t s, const Tuning& tu) {
+cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* ws, cudaStream_t s,
+                       const Tuning& tu) {
+  uint16_t* g = reinterpret_cast<uint16_t*>(ws);
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + align_up((size_t)d.n * sizeof(uint16_t)));
   const uint32_t nrows = (uint32_t)d.ny * (uint32_t)d.nz;
   const unsigned blocks = (nrows + 7) / 8;
   {
     TraceScope t("edt_rows_x", s);
     if (d.nx % 16 == 0)
-      edt_rows_kernel<true><<<blocks, 256, 0, s>>>(mask, dt2, d.nx, nrows);
+      edt_rows_kernel<true><<<blocks, 256, 0, s>>>(mask, g, d.nx, nrows);
     else
-      edt_rows_kernel<false><<<blocks, 256, 0, s>>>(mask, dt2, d.nx, nrows);
+      edt_rows_kernel<false><<<blocks, 256, 0, s>>>(mask, g, d.nx, nrows);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t plane = (size_t)d.nx * d.ny;
-  // y: columns of length ny, stride nx; one tile row per z.
-  e = col_pass("edt_cols_y", dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s, tu.edt_tx_small);
+  // y: columns of length ny, stride nx; one tile row per z; g -> dt2.
+  e = col_pass<uint16_t>("edt_cols_y", g, dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s,
+                         tu.edt_tx_y);
   if (e != cudaSuccess || d.ndim == 2) return e;
-  // z: columns of length nz, stride nx*ny; one tile row per y.
-  return col_pass("edt_cols_z", dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s, tu.edt_tx_small);
+  // z: columns of length nz, stride nx*ny; one tile row per y; in place.
+  return col_pass<uint32_t>("edt_cols_z", dt2, dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s,
+                            tu.edt_tx_z);
 }
 
 }  // namespace ltk

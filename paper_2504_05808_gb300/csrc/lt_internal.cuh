@@ -57,7 +57,8 @@ struct ShapeAcc {
 // Launch parameters the batch autotuner may change (defaults: single calls).
 // Defaults: the autotuner's choice for the 512^3 particle volume on GB300.
 struct Tuning {
-  int edt_tx_small = 16;        // EDT column-tile width for axes <= 512 (32 or 16)
+  int edt_tx_y = 8;             // EDT column-tile width of the y pass for axes <= 512 (32, 16 or 8)
+  int edt_tx_z = 16;            // and of the z pass (its tile rows are a plane apart)
   int ridge_z = 32;             // z planes per ridge CTA (8, 16 or 32)
   int paint_blocks_per_sm = 6;  // persistent paint grid, CTAs per SM
 };
@@ -66,8 +67,8 @@ struct Tuning {
 // edt.cu
 size_t edt_workspace_bytes(const Dims& d);
 cudaError_t edt_prepare_device();  // kernel attributes; call before capture
-cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, uint32_t* tmp,
-                       cudaStream_t s, const Tuning& tu = Tuning());
+cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* ws, cudaStream_t s,
+                       const Tuning& tu = Tuning());
 // lt.cu
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,

@@ -50,8 +50,10 @@ def test_workspace_sizes(lt):
     # local thickness: header + 16 bytes per voxel (centre records)
     ws = L.lt_local_thickness_workspace_size(3, 512, 512, 512)
     assert 16 * n <= ws < 16 * n + 4096
-    assert L.lt_edt_workspace_size(3, 512, 512, 512) == 0
-    assert L.lt_edt_workspace_size(2, 100, 3000, 1) == 4 * 300000
+    # EDT: 16-bit row distances, plus uint32 per voxel for z axes over 2048
+    assert L.lt_edt_workspace_size(3, 512, 512, 512) == 2 * n
+    assert L.lt_edt_workspace_size(2, 100, 3000, 1) == -(-2 * 300000 // 256) * 256  # 256-byte aligned
+    assert L.lt_edt_workspace_size(3, 16, 16, 3000) == 2 * 768000 + 4 * 768000
     assert L.lt_shape_workspace_size(1000) >= 28 * 1000
     assert L.lt_measure_workspace_size(100, 3, 512, 512, 512) >= ws
     host = L.lt_measure_host_workspace_size(100, 3, 64, 64, 64)

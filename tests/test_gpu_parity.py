@@ -126,7 +126,7 @@ def test_long_axes_use_every_column_path(lt):
     and the global-memory column pass."""
     import scipy.ndimage as ndi
     rng = np.random.default_rng(3)
-    for shape in [(700, 37), (1500, 21), (2500, 9), (600, 20, 24), (1100, 9, 17)]:
+    for shape in [(700, 37), (1500, 21), (2500, 9), (600, 20, 24), (1100, 9, 17), (2100, 6, 8)]:
         f = ndi.gaussian_filter(rng.random(shape), 4.0)
         mask = (f > np.quantile(f, 0.3)).astype(np.uint8)
         labels = ndi.label(mask)[0].astype(np.uint32)
