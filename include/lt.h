@@ -320,6 +320,17 @@ typedef struct lt_lt_counters {
 } lt_lt_counters;
 lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, lt_lt_counters* out);
 
+/* Self-test of failure detection: runs the local-thickness ridge kernel
+ * (the one kernel that waits, on its shared-memory copies) on a 32 x 8 x 8
+ * all-background volume carved from `ws`, with every copy barrier expecting
+ * 16 bytes more than its copies deliver, so that each wait reaches its limit
+ * (1 ms here). The kernel records the timeout in `ws` and returns; this
+ * function waits for `stream` and returns what lt_workspace_status reads:
+ * LT_ERR_TIMEOUT when the limit works. No copy is left in flight and the
+ * context stays usable. Workspace: lt_selftest_workspace_size() bytes. */
+size_t lt_selftest_workspace_size(void);
+lt_status lt_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------ calibration --
  * Measures this GPU's rate of 32-bit atomic-max updates to global memory,
  * the operation the painting step consists of, as a ceiling to compare

@@ -45,6 +45,8 @@ SIGNATURES = {
     "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
     "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
     "lt_workspace_counters": (_i32, [_vp, _sz, _vp, _vp]),
+    "lt_selftest_workspace_size": (_sz, []),
+    "lt_selftest_wait_timeout": (_i32, [_vp, _sz, _vp]),
     "lt_probe_update_rate": (_i32, [_vp, _sz, _i32, _i32, _vp, _vp]),
     "lt_shape_measures_static": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp]),
     "lt_features_workspace_size": (_sz, [_u32]),
@@ -232,6 +234,13 @@ def lt_workspace_counters(ws, stream=None):
            "workspace counters")
     return {"chunk_centres": c.chunk_centres, "warp_centres": c.warp_centres, "updates": c.updates,
             "table_updates": c.table_updates}
+
+
+def lt_selftest_wait_timeout(device="cuda", stream=None):
+    """Runs the bounded-wait self-test (see include/lt.h) and returns the
+    device status it produced: LT_ERR_TIMEOUT (8) when the wait limit works."""
+    ws = workspace(lib.lt_selftest_workspace_size(), device)
+    return lib.lt_selftest_wait_timeout(_ptr(ws), ws.numel(), _stream(stream))
 
 
 def lt_probe_update_rate(buf, pattern, reps=5, stream=None):

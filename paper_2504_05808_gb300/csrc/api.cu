@@ -290,6 +290,15 @@ lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
   return LT_OK;
 }
 
+size_t lt_selftest_workspace_size(void) { return ridge_selftest_bytes(); }
+
+lt_status lt_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream) {
+  lt_status st = check_ws(ws, ws_bytes, ridge_selftest_bytes());
+  if (st != LT_OK) return st;
+  if (ridge_selftest_launch(ws, as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
+  return lt_workspace_status(ws, ws_bytes, stream);
+}
+
 lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, lt_lt_counters* out) {
   if (!ws || ws_bytes < sizeof(WsHeader) || !aligned(ws, kAlign)) return LT_ERR_WORKSPACE;
   if (!out) return LT_ERR_INVALID_ARG;

@@ -240,6 +240,14 @@ constexpr int kListBuf = 256 * kRidgeFlush;
 constexpr uint32_t kPlaneBytes = kBX * kBY * 4;
 static_assert(kSlotPitch * 4 % 128 == 0 && kSlotPitch >= kBX * kBY, "slot layout");
 
+// Wait: the time limit of each plane wait. extra_tx: bytes each plane's
+// barrier expects beyond its two copies, 0 except in the timeout self-test,
+// where it makes every wait reach its limit.
+struct RidgeWait {
+  uint64_t limit_ns = kWaitNs;
+  uint32_t extra_tx = 0;
+};
+
 template <int NDIM, int RZ, bool TMA>
 __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ CUtensorMap map_dt2,
                                                        const __grid_constant__ CUtensorMap map_lab,
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
                                                        uint4* __restrict__ surv,
-                                                       WsHeader* __restrict__ hdr) {
+                                                       WsHeader* __restrict__ hdr, RidgeWait wt) {
   __shared__ __align__(128) uint32_t sD[kSlots][kSlotPitch];
   __shared__ __align__(128) uint32_t sL[kSlots][kSlotPitch];
   __shared__ uint4 buf[kListBuf];
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   auto parity_of = [&](int p) { return (uint32_t)(((p - z0 + 1) >> 2) & 1); };
   auto issue = [&](int p) {
     const int s = slot_of(p);
-    mbar_expect_tx(&bar[s], 2 * kPlaneBytes);
+    mbar_expect_tx(&bar[s], 2 * kPlaneBytes + wt.extra_tx);
     tma_load_3d(sD[s], &map_dt2, x0 - kOX, y0 - 1, p, &bar[s]);
     tma_load_3d(sL[s], &map_lab, x0 - kOX, y0 - 1, p, &bar[s]);
   };
@@ -312,8 +320,10 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   for (int z = z0; z < z1; ++z) {
     bool ok = true;
     if (TMA) {
-      if (z == z0) ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1)) && mbar_wait(&bar[slot_of(z)], parity_of(z));
-      ok = ok && mbar_wait(&bar[slot_of(z + 1)], parity_of(z + 1));
+      if (z == z0)
+        ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1), wt.limit_ns) &&
+             mbar_wait(&bar[slot_of(z)], parity_of(z), wt.limit_ns);
+      ok = ok && mbar_wait(&bar[slot_of(z + 1)], parity_of(z + 1), wt.limit_ns);
     } else if (NDIM == 3) {
       load_plane(z + 1);
     }
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       // bounded) for the copies this CTA still has in flight, and stop
       if (tid == 0) {
         atomicOr(&hdr->error, ERR_TIMEOUT);
-        for (int p = z - 1; p <= min(z1, z + 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p));
+        for (int p = z - 1; p <= min(z1, z + 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p), wt.limit_ns);
       }
       return;
     }
@@ -884,11 +894,11 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
 template <int NDIM, int RZ>
 void launch_ridge(bool tma, dim3 grid, cudaStream_t s, const CUtensorMap& md, const CUtensorMap& ml,
                   const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d, uint4* surv,
-                  WsHeader* hdr) {
+                  WsHeader* hdr, RidgeWait wt = RidgeWait()) {
   if (tma)
-    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr);
+    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt);
   else
-    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr);
+    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt);
 }
 
 }  // namespace
@@ -916,6 +926,40 @@ bool make_tensor_map_u32_3d(CUtensorMap* map, const void* base, int nx, int ny, 
 size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint4)); }
 
 cudaError_t lt_prepare_device() { return ensure_tables(); }
+
+// Timeout self-test: the TMA ridge kernel on a 32 x 8 x 8 all-background
+// volume carved from `ws`, with every plane barrier expecting 16 bytes more
+// than its copies deliver, so each wait gives up after 1 ms; the kernel must
+// record ERR_TIMEOUT in the header and return.
+size_t ridge_selftest_bytes() { return sizeof(WsHeader) + 2048 * (3 * 4 + 16); }
+
+cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s) {
+  cudaError_t e = ensure_tables();
+  if (e != cudaSuccess) return e;
+  Dims d;
+  d.ndim = 3;
+  d.nx = 32;
+  d.ny = 8;
+  d.nz = 8;
+  d.n = 2048;
+  char* p = reinterpret_cast<char*>(ws);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(p);
+  uint32_t* dt2 = reinterpret_cast<uint32_t*>(p + sizeof(WsHeader));
+  uint32_t* labels = dt2 + d.n;
+  uint32_t* lt2 = labels + d.n;
+  uint4* surv = reinterpret_cast<uint4*>(lt2 + d.n);
+  e = cudaMemsetAsync(ws, 0, sizeof(WsHeader) + 3 * 4 * (size_t)d.n, s);
+  if (e != cudaSuccess) return e;
+  CUtensorMap md, ml;
+  if (!make_tensor_map_u32_3d(&md, dt2, d.nx, d.ny, d.nz, kBX, kBY) ||
+      !make_tensor_map_u32_3d(&ml, labels, d.nx, d.ny, d.nz, kBX, kBY))
+    return cudaErrorInvalidValue;
+  RidgeWait wt;
+  wt.limit_ns = 1000000ull;
+  wt.extra_tx = 16;
+  launch_ridge<3, 32>(true, dim3(1, 1, 1), s, md, ml, dt2, labels, lt2, d, surv, hdr, wt);
+  return cudaGetLastError();
+}
 
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {

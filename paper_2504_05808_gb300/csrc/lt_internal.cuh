@@ -73,6 +73,9 @@ cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* 
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu = Tuning());
+// timeout self-test of the ridge kernel's bounded waits (see lt.h)
+size_t ridge_selftest_bytes();
+cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);
 // copies the lookup tables to the current device (first use); call before capture
 cudaError_t lt_prepare_device();
 // shape.cu

@@ -10,9 +10,10 @@
 
 namespace ltk {
 
-// Limits of every mbarrier wait: one second of %globaltimer, and an
-// iteration cap as a second bound. A real copy lands within microseconds;
-// the limits only keep a copy that never completes from hanging the GPU.
+// Limits of every mbarrier wait: a time budget of %globaltimer (one second
+// unless the caller asks for less), and an iteration cap as a second bound.
+// A real copy lands within microseconds; the limits only keep a copy that
+// never completes from hanging the GPU.
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -56,12 +57,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t i = 0; i < kWaitLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 63u && globaltimer_ns() - t0 > kWaitNs) return false;
+    if ((i & 63u) == 63u && globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
