@@ -72,10 +72,11 @@ constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
 __device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
 __device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
-__device__ uint32_t g_cres_start[kCresMaxCombos + 1];
-// the same crescents with another canonical axis innermost: y for class 1,
-// z for class 2 (class 3: same as g_cres_start); the size is the same
-__device__ uint32_t g_cres_start_alt[kCresMaxCombos];
+// per combination: x = first voxel | size << 22, y = first voxel of the same
+// crescent in the alternative order below
+__device__ uint2 g_cres_combo[kCresMaxCombos];
+// (the same crescents with another canonical axis innermost: y for class 1,
+// z for class 2; class 3 has one order)
 // canonical crescent voxels: (x+128) | (y+128) << 8 | (z+128) << 16 |
 // (on the sphere |y|^2 == r^2) << 24
 __device__ uint32_t g_cres_vox[kCresMaxVoxels];
@@ -83,6 +84,7 @@ __device__ uint32_t g_cres_vox[kCresMaxVoxels];
 // ------------------------------------------------------------ host tables
 struct HostTables {
   std::vector<uint32_t> m3, m2, base, start, start_alt, vox;
+  std::vector<uint2> combo;
   bool ok = false;
 };
 
@@ -168,6 +170,8 @@ HostTables* build_host_tables() {
   // table records hold a crescent's first voxel in 22 bits and its size in 10
   for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 1024u;
   t->ok = t->ok && t->vox.size() < (1u << 22);
+  for (size_t i = 0; i + 1 < t->start.size(); ++i)
+    t->combo.push_back(make_uint2(t->start[i] | ((t->start[i + 1] - t->start[i]) << 22), t->start_alt[i]));
   return t;
 }
 
@@ -189,15 +193,14 @@ cudaError_t ensure_tables() {
   e = cudaMemcpyToSymbol(g_m3, h.m3.data(), h.m3.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_m2, h.m2.data(), h.m2.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_base, h.base.data(), h.base.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_start, h.start.data(), h.start.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_start_alt, h.start_alt.data(), h.start_alt.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_combo, h.combo.data(), h.combo.size() * sizeof(uint2));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_vox, h.vox.data(), h.vox.size() * 4);
   if (e == cudaSuccess) g_tables_on[dev] = true;
   return e;
 }
 
-__device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd2) {
-  return g_cres_base[cls * (kCresT + 1) + r2] + (rd2 - r2);
+__device__ __forceinline__ uint32_t cres_combo(const uint32_t* base, int cls, uint32_t r2, uint32_t rd2) {
+  return base[cls * (kCresT + 1) + r2] + (rd2 - r2);
 }
 
 // ---------------------------------------------------------- ridge kernel
@@ -216,7 +219,9 @@ __device__ __forceinline__ uint32_t cres_combo(int cls, uint32_t r2, uint32_t rd
 // the 26-neighbour (8 in 2D) test runs on full warps; every neighbour is
 // evaluated without early exit. Kept centres collect in one shared buffer
 // (front list from its front, back list from its back) and leave with one
-// global atomic per list every kRidgeFlush planes. The front of `surv` gets
+// global atomic per list whenever another plane might not fit (every ~12
+// planes at 512^3: the two list counters are hot, one atomic per flush
+// keeps them from serialising the CTAs). The front of `surv` gets
 // the centres painted in shared chunks: 3D centres with r^2 <= kCresT, a
 // dominant neighbour and a crescent of at most kChunkCres voxels, and every
 // 2D centre. The back gets those a warp paints alone: bigger crescents and
@@ -235,8 +240,7 @@ constexpr int kOX = 4;                             // halo column of x0 (keeps T
 constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 40 x 10 words
 constexpr int kSlotPitch = 416;                    // words per slot: 40 x 10 rounded up to 128 bytes
 constexpr int kSlots = 4;
-constexpr int kRidgeFlush = 2;
-constexpr int kListBuf = 256 * kRidgeFlush;
+constexpr int kListBuf = 512;  // kept centres buffered per CTA (a plane adds at most 256)
 constexpr uint32_t kPlaneBytes = kBX * kBY * 4;
 static_assert(kSlotPitch * 4 % 128 == 0 && kSlotPitch >= kBX * kBY, "slot layout");
 
@@ -262,6 +266,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   __shared__ uint16_t work[256];
   __shared__ __align__(8) uint64_t bar[kSlots];
   __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s;
+  __shared__ uint32_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 1];  // copy of g_cres_base
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int z0 = NDIM == 3 ? blockIdx.z * RZ : 0;
@@ -294,6 +299,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       sL[s][hy * kBX + hx + kOX - 1] = lv;
     }
   };
+  if (NDIM == 3)
+    for (int i = tid; i < 3 * (kCresT + 1); i += 256) sbase[i] = g_cres_base[i];
   if (tid == 0) {
     cntA = cntB = 0;
     // after a timeout anywhere in this launch, the remaining CTAs stop at once
@@ -417,22 +424,26 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
         }
       }
       if (!pruned) {
-        uint32_t code = kNoDominant, bcomb = 0, best = UINT_MAX;
+        uint32_t code = kNoDominant, vstart = 0, best = UINT_MAX;
         int kd = -1;
         if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
-          // the candidate whose crescent has the fewest voxels
+          // the candidate whose crescent has the fewest voxels; its voxels
+          // in the order with world x innermost (the alternative order when
+          // the offset has no x component)
+          uint2 ce[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k)
-            if (brn[k] >= 0) {
-              const uint32_t cb = cres_combo(k, r2, (uint32_t)brn[k]);
-              const uint32_t s0 = g_cres_start[cb], sz = g_cres_start[cb + 1] - s0;
-              if (sz < best) {
-                best = sz;
-                bcomb = cb;
-                code = bcode[k];
-                kd = k;
-              }
+            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(~0u, 0u);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const uint32_t sz = ce[k].x >> 22;
+            if (brn[k] >= 0 && sz < best) {
+              best = sz;
+              vstart = bcode[k] % 3 == 1 ? ce[k].y : ce[k].x & 0x3FFFFFu;
+              code = bcode[k];
+              kd = k;
             }
+          }
         } else {
           // the candidate whose ball comes closest to containing c's
           int best = INT_MIN;
@@ -456,9 +467,6 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           }
         const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
         if (NDIM == 3 && tab) {
-          // crescent order with world x innermost: the alternative order
-          // when the dominant offset has no x component
-          const uint32_t vstart = code % 3 == 1 ? g_cres_start_alt[bcomb] : g_cres_start[bcomb];
           const int R = (int)isqrt24(r2);
           const int x = x0 + tx, y = y0 + ty;
           const uint32_t inside = x >= R && x + R < d.nx && y >= R && y + R < d.ny && z >= R && z + R < d.nz;
@@ -472,8 +480,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
         keepB = !keepA;
       }
     }
-    // at most 256 * kRidgeFlush records between flushes: list A grows from
-    // the front of buf, list B from its back
+    // at most kListBuf records between flushes: list A grows from the front
+    // of buf, list B from its back
     const unsigned ba = __ballot_sync(kFull, keepA), bb = __ballot_sync(kFull, keepB);
     if (ba) {
       uint32_t wb = 0;
@@ -493,7 +501,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       issue(z + 3);
     }
     if (tid == 0) nwork_s = 0;
-    if ((z - z0) % kRidgeFlush == kRidgeFlush - 1 || z + 1 == z1) {
+    if (cntA + cntB > kListBuf - 256 || z + 1 == z1) {  // uniform: read after the barrier
       if (tid == 0) {
         baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
         baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
