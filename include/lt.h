@@ -150,6 +150,33 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
                             float* sphericity, float* roundness, const lt_object_stats* stats,
                             void* stream);
 
+/* ---------------------------------------------- post-processing of R, S --
+ * lt_shape_measures_filtered: lt_shape_measures after roughness filtering.
+ *   The paper expects surface roughness to be controllable by filtering
+ *   the contour/surface (Sec. 7) and names no filter; this library's filter
+ *   keeps, of every object, the voxels whose local thickness is at least
+ *   sqrt(min_lt2), i.e. the union of its inscribed balls of squared radius
+ *   >= min_lt2 (an opening of the object by a ball), and measures S, R and
+ *   the sums on what remains: voxels below the threshold count as outside
+ *   their object (also for the shell test). Features thinner than the
+ *   threshold radius disappear; objects entirely below it give NaN.
+ *   min_lt2 <= 1 filters nothing (every object voxel has LT2 >= 1), so the
+ *   result equals lt_shape_measures. Same arguments, workspace and errors.
+ * lt_roundness_rescale: R_LT never exceeds 1 and stays above 0 (Sec. 6.1);
+ *   with its minimum m it maps onto 0-1: out = max(0, (R - m) / (1 - m)).
+ *   m = r_min when r_min >= 0 (a reference minimum, e.g. from another
+ *   population; values below it map to 0), else the smallest finite value
+ *   of roundness[0..n). NaN stays NaN; m >= 1 gives 1. Device arrays of n
+ *   floats (out may alias roundness); workspace:
+ *   lt_roundness_rescale_workspace_size() bytes. r_min NaN is rejected. */
+lt_status lt_shape_measures_filtered(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                                     uint32_t min_lt2, int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws,
+                                     size_t ws_bytes, float* sphericity, float* roundness,
+                                     const lt_object_stats* stats, void* stream);
+size_t lt_roundness_rescale_workspace_size(void);
+lt_status lt_roundness_rescale(const float* roundness, uint32_t n, float r_min, float* out, void* ws,
+                               size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------- batched form --
  * Many volumes (2D and 3D, uneven sizes) measured as one unit of work. The
  * batch owns no device memory: `ws` (lt_batch_workspace_size bytes) holds

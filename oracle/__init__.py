@@ -22,6 +22,9 @@ and 3D using Local Thickness"):
   sphericity_2d        Eqs. 2, 9-11: ellipse with a = mean LT, b = A/(pi a);
                        Ramanujan's perimeter P_o and P_c = 2 sqrt(pi A).
   roundness            Sec. 4.2: mean LT on the shell / max LT.
+  measures_filtered    roughness filtering (Sec. 7: filter left open; read
+                       as keeping each object's voxels with LT >= rho).
+  roundness_rescaled   R mapped to 0-1 with the reported minimum (Sec. 6.1).
 
 Readings where the paper is garbled or silent (each is listed in the design doc):
   * Eqs. 6-7 print e = 1 - c^2/a^2 without a square root; the spheroid's
@@ -292,6 +295,33 @@ def object_measures_from_voxels(labels: np.ndarray, idx: np.ndarray, lt2_vals: n
     S = sphericity_3d(V, mean_lt) if lab.ndim == 3 else sphericity_2d(V, mean_lt)
     R = roundness(lt[shell].sum(), int(shell.sum()), int(np.max(lt2_vals)))
     return S, R
+
+
+def measures_filtered(labels: np.ndarray, lt2_arr: np.ndarray, n_labels: int, min_lt2: int):
+    """S and R after roughness filtering (Sec. 7 leaves the filter open; this
+    is the reading used): each object is reduced to its voxels whose local
+    thickness is at least sqrt(min_lt2), i.e. to the union of its inscribed
+    balls of squared radius >= min_lt2, and S, R are measured on what
+    remains (shell and sums by the same definitions). Empty objects give NaN."""
+    lab = np.asarray(labels)
+    kept = np.where(np.asarray(lt2_arr).astype(np.int64) >= int(min_lt2), lab, 0)
+    return measures(kept, lt2_arr, n_labels)
+
+
+def roundness_rescaled(R: np.ndarray, r_min: float | None = None) -> np.ndarray:
+    """Roundness mapped to the 0-1 range with the reported minimum (Sec. 6.1
+    remarks that R_LT never exceeds 1 and never reaches 0, and that the
+    minimum can map it onto 0-1): R' = (R - m) / (1 - m), m = r_min or the
+    smallest finite R; clamped below at 0; NaN stays NaN; 1 when m >= 1."""
+    R = np.asarray(R, dtype=np.float64)
+    fin = np.isfinite(R)
+    m = float(np.min(R[fin])) if r_min is None else float(r_min)
+    out = np.full(R.shape, np.nan)
+    if m >= 1.0:
+        out[fin] = 1.0
+    else:
+        out[fin] = np.maximum((R[fin] - m) / (1.0 - m), 0.0)
+    return out
 
 
 def pipeline(mask: np.ndarray, labels: np.ndarray, n_labels: int):

@@ -39,6 +39,9 @@ SIGNATURES = {
     "lt_local_thickness": (_i32, [_vp, _vp, _vp] + _DIMS + [_vp, _sz, _vp]),
     "lt_shape_workspace_size": (_sz, [_u32]),
     "lt_shape_measures": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp]),
+    "lt_shape_measures_filtered": (_i32, [_vp, _vp, _u32, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp]),
+    "lt_roundness_rescale_workspace_size": (_sz, []),
+    "lt_roundness_rescale": (_i32, [_vp, _u32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "lt_measure_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
     "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
@@ -168,6 +171,31 @@ def lt_shape_measures(labels, lt2, n_labels, sphericity=None, roundness=None, st
                                  ctypes.byref(st) if st is not None else None, _stream(stream)),
            "lt_shape_measures")
     return ws
+
+
+def lt_shape_measures_filtered(labels, lt2, n_labels, min_lt2, sphericity=None, roundness=None,
+                               stats=None, ws=None, stream=None):
+    """lt_shape_measures on the objects reduced to their voxels with
+    LT2 >= min_lt2 (roughness filtering; see include/lt.h)."""
+    nd, nx, ny, nz = _dims(labels)
+    if ws is None:
+        ws = workspace(lib.lt_shape_workspace_size(n_labels), labels.device)
+    st = None
+    if stats is not None:
+        st = ObjectStats(*[stats[k].data_ptr() if k in stats else None
+                           for k in ("volume", "n_shell", "max_lt2", "sum_lt", "sum_shell_lt")])
+    _check(lib.lt_shape_measures_filtered(_ptr(labels), _ptr(lt2), n_labels, int(min_lt2), nd, nx, ny, nz,
+                                          _ptr(ws), ws.numel(), _ptr(sphericity), _ptr(roundness),
+                                          ctypes.byref(st) if st is not None else None, _stream(stream)),
+           "lt_shape_measures_filtered")
+    return ws
+
+
+def lt_roundness_rescale(roundness, out, r_min=None, stream=None):
+    """out = max(0, (R - m) / (1 - m)), m = r_min or the smallest finite R."""
+    ws = workspace(lib.lt_roundness_rescale_workspace_size(), roundness.device)
+    _check(lib.lt_roundness_rescale(_ptr(roundness), roundness.numel(), -1.0 if r_min is None else float(r_min),
+                                    _ptr(out), _ptr(ws), ws.numel(), _stream(stream)), "lt_roundness_rescale")
 
 
 def lt_measure(mask, labels, n_labels, dt2, lt2, sphericity, roundness, ws=None, stream=None):

@@ -186,6 +186,14 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
                             int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
                             float* sphericity, float* roundness, const lt_object_stats* stats,
                             void* stream) {
+  return lt_shape_measures_filtered(labels, lt2, n_labels, 0u, ndim, nx, ny, nz, ws, ws_bytes, sphericity,
+                                    roundness, stats, stream);
+}
+
+lt_status lt_shape_measures_filtered(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                                     uint32_t min_lt2, int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws,
+                                     size_t ws_bytes, float* sphericity, float* roundness,
+                                     const lt_object_stats* stats, void* stream) {
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
@@ -202,7 +210,8 @@ lt_status lt_shape_measures(const uint32_t* labels, const uint32_t* lt2, uint32_
   cudaStream_t s = as_stream(stream);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
   cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
-  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, hdr + 1, sphericity, roundness, stats, s);
+  if (e == cudaSuccess)
+    e = shape_launch(labels, lt2, n_labels, d, hdr, hdr + 1, sphericity, roundness, stats, s, min_lt2);
   return cuda_status(e);
 }
 
@@ -288,6 +297,18 @@ lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
   if (err & ERR_LABEL_OUTSIDE_MASK) return LT_ERR_LABEL_OUTSIDE_MASK;
   if (err & ERR_LABEL_RANGE) return LT_ERR_LABEL_RANGE;
   return LT_OK;
+}
+
+size_t lt_roundness_rescale_workspace_size(void) { return kAlign; }
+
+lt_status lt_roundness_rescale(const float* roundness, uint32_t n, float r_min, float* out, void* ws,
+                               size_t ws_bytes, void* stream) {
+  if (n == 0) return LT_OK;
+  lt_status st;
+  if ((st = dev_ptr(roundness)) != LT_OK || (st = dev_ptr(out)) != LT_OK) return st;
+  if (!(r_min < 1.f) && !(r_min >= 1.f)) return LT_ERR_INVALID_ARG;  // NaN
+  if ((st = check_ws(ws, ws_bytes, kAlign)) != LT_OK) return st;
+  return cuda_status(rescale_launch(roundness, n, r_min, reinterpret_cast<uint32_t*>(ws), out, as_stream(stream)));
 }
 
 size_t lt_selftest_workspace_size(void) { return ridge_selftest_bytes(); }

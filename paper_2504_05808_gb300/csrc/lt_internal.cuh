@@ -80,9 +80,13 @@ cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);
 cudaError_t lt_prepare_device();
 // shape.cu
 size_t shape_workspace_bytes(uint32_t n_labels);
+// roundness mapped to 0-1; r_min < 0: the smallest finite value (scratch: 4 bytes)
+cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* scratch, float* out,
+                           cudaStream_t s);
+// min_lt2 > 1: the objects are reduced to their voxels with LT2 >= min_lt2
 cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
-                         const lt_object_stats* stats, cudaStream_t s);
+                         const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2 = 0);
 
 // learned.cu
 size_t features_workspace_bytes(uint32_t n_labels);

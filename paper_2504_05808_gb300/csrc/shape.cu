@@ -28,11 +28,21 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFixScale = 1048576.0f;  // 2^LT_FIXED_POINT_SHIFT
 
-template <int NDIM>
+// Object label of voxel v as the reduction sees it: with FILTER, voxels
+// whose LT2 is below min_lt2 are outside every object (the object is the
+// union of its inscribed balls with r^2 >= min_lt2).
+template <bool FILTER>
+__device__ __forceinline__ uint32_t obj_label(const uint32_t* __restrict__ labels,
+                                              const uint32_t* __restrict__ lt2, size_t v, uint32_t min_lt2) {
+  const uint32_t l = labels[v];
+  return FILTER && l && lt2[v] < min_lt2 ? 0u : l;
+}
+
+template <int NDIM, bool FILTER>
 __global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __restrict__ labels,
                                                            const uint32_t* __restrict__ lt2, Dims d,
                                                            uint32_t n_labels, ShapeAcc acc,
-                                                           WsHeader* __restrict__ hdr) {
+                                                           WsHeader* __restrict__ hdr, uint32_t min_lt2) {
   const int lane = threadIdx.x & 31;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -44,15 +54,17 @@ __global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __res
   const bool bad = l >= n_labels;
   if (__any_sync(kFull, bad) && lane == 0) atomicOr(&hdr->error, ERR_LABEL_RANGE);
   if (bad) l = 0;
+  if (FILTER && l && lt2[v] < min_lt2) l = 0;
 
   uint32_t pk = 0, mx = 0;  // pk = count | shell count << 16
   unsigned long long q = 0, qs = 0;
   if (l) {
     const uint32_t t = lt2[v];
     const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
-    bool s = x == 0 || labels[v - 1] != l || x == d.nx - 1 || labels[v + 1] != l || y == 0 ||
-             labels[v - sy] != l || y == d.ny - 1 || labels[v + sy] != l;
-    if (NDIM == 3) s = s || z == 0 || labels[v - sz] != l || z == d.nz - 1 || labels[v + sz] != l;
+    auto nb = [&](size_t u) { return obj_label<FILTER>(labels, lt2, u, min_lt2); };
+    bool s = x == 0 || nb(v - 1) != l || x == d.nx - 1 || nb(v + 1) != l || y == 0 || nb(v - sy) != l ||
+             y == d.ny - 1 || nb(v + sy) != l;
+    if (NDIM == 3) s = s || z == 0 || nb(v - sz) != l || z == d.nz - 1 || nb(v + sz) != l;
     pk = 1u | (s ? 1u << 16 : 0u);
     mx = t;
     q = qq;
@@ -98,11 +110,19 @@ __device__ __forceinline__ uint32_t comp(const uint4& v, int k) {
   return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-template <int NDIM>
+// Four labels of a row with those whose LT2 is below min_lt2 set to 0.
+__device__ __forceinline__ uint4 filter4(uint4 L, const uint32_t* __restrict__ lt2, size_t v, uint32_t min_lt2) {
+  if ((L.x | L.y | L.z | L.w) == 0u) return L;
+  const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
+  return make_uint4(T.x < min_lt2 ? 0u : L.x, T.y < min_lt2 ? 0u : L.y, T.z < min_lt2 ? 0u : L.z,
+                    T.w < min_lt2 ? 0u : L.w);
+}
+
+template <int NDIM, bool FILTER>
 __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
                                                             const uint32_t* __restrict__ lt2, Dims d,
                                                             uint32_t n_labels, ShapeAcc acc,
-                                                            WsHeader* __restrict__ hdr) {
+                                                            WsHeader* __restrict__ hdr, uint32_t min_lt2) {
   const int lane = threadIdx.x & 31;
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
@@ -119,23 +139,37 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
   if (any) {
     const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    const uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
-    const uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
+    uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
+    uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
     uint4 Zm = zero, Zp = zero;
     if (NDIM == 3) {
       if (z > 0) Zm = *reinterpret_cast<const uint4*>(labels + v - sz);
       if (z + 1 < d.nz) Zp = *reinterpret_cast<const uint4*>(labels + v + sz);
     }
-    const uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
-    const uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
+    uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
+    uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
+    if (FILTER) {  // neighbours below the threshold are outside their object
+      if (y > 0) Ym = filter4(Ym, lt2, v - sy, min_lt2);
+      if (y + 1 < d.ny) Yp = filter4(Yp, lt2, v + sy, min_lt2);
+      if (NDIM == 3 && z > 0) Zm = filter4(Zm, lt2, v - sz, min_lt2);
+      if (NDIM == 3 && z + 1 < d.nz) Zp = filter4(Zp, lt2, v + sz, min_lt2);
+      if (xl && lt2[v - 1] < min_lt2) xl = 0u;
+      if (xr && lt2[v + 4] < min_lt2) xr = 0u;
+    }
+    uint4 Lf = L;  // labels as objects: range-checked raw labels, filtered
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t l = comp(L, k);
+      if (l >= n_labels) bad = true;
+      const uint32_t lf = l >= n_labels || (FILTER && comp(T, k) < min_lt2) ? 0u : l;
+      Lf = make_uint4(k == 0 ? lf : Lf.x, k == 1 ? lf : Lf.y, k == 2 ? lf : Lf.z, k == 3 ? lf : Lf.w);
+    }
+    if (FILTER) L = Lf;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       uint32_t l = comp(L, k);
       if (l == 0) continue;
-      if (l >= n_labels) {
-        bad = true;
-        continue;
-      }
+      if (l >= n_labels) continue;
       const uint32_t left = k == 0 ? xl : comp(L, k - 1), right = k == 3 ? xr : comp(L, k + 1);
       bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l;
       if (NDIM == 3) s = s || comp(Zm, k) != l || comp(Zp, k) != l;
@@ -234,7 +268,49 @@ __global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __
   if (R) R[l] = (float)rnd;
 }
 
+// Roundness mapped to 0-1 with the reported minimum (Sec. 6.1). Step 1:
+// the smallest finite R over [0, n) by warp minima and one atomic per warp
+// (R > 0, so the float bits order like the values). Step 2: the map.
+__global__ void min_finite_kernel(const float* __restrict__ R, uint32_t n, uint32_t* __restrict__ out_bits) {
+  uint32_t m = 0x7F800000u;  // +inf (out_bits starts at 0xFFFFFFFF: no finite value)
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float r = R[i];
+    if (isfinite(r) && r >= 0.f) m = min(m, __float_as_uint(r));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m != 0x7F800000u) atomicMin(out_bits, m);
+}
+
+__global__ void rescale_kernel(const float* __restrict__ R, uint32_t n, const uint32_t* __restrict__ min_bits,
+                               float r_min, float* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float r = R[i];
+  const double m = r_min >= 0.f ? (double)r_min : (double)__uint_as_float(*min_bits);
+  float v = nanf("");
+  if (isfinite(r)) v = m >= 1.0 ? 1.f : (float)fmax(((double)r - m) / (1.0 - m), 0.0);
+  out[i] = v;
+}
+
 }  // namespace
+
+cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* scratch, float* out,
+                           cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (r_min < 0.f) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0xFF, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<uint32_t>((n + 255) / 256, (uint32_t)sm_count() * 4u);
+    TraceScope t("roundness_min", s);
+    min_finite_kernel<<<blocks, 256, 0, s>>>(R, n, scratch);
+  }
+  {
+    TraceScope t("roundness_rescale", s);
+    rescale_kernel<<<(n + 255) / 256, 256, 0, s>>>(R, n, scratch, r_min, out);
+  }
+  return cudaGetLastError();
+}
 
 static size_t acc_bytes(uint32_t n) {
   return 3 * align_up((size_t)n * 4) + 2 * align_up((size_t)n * 8);
@@ -242,9 +318,23 @@ static size_t acc_bytes(uint32_t n) {
 
 size_t shape_workspace_bytes(uint32_t n_labels) { return acc_bytes(n_labels); }
 
+template <int NDIM, bool FILTER>
+void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                   const ShapeAcc& acc, WsHeader* hdr, uint32_t min_lt2, cudaStream_t s) {
+  TraceScope t("shape_reduce", s);
+  if (d.nx % 4 == 0) {
+    // 64 threads (256 voxels) per row, 4 rows per CTA
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    shape_reduce4_kernel<NDIM, FILTER><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2);
+  } else {
+    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
+    shape_reduce_kernel<NDIM, FILTER><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2);
+  }
+}
+
 cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
-                         const lt_object_stats* stats, cudaStream_t s) {
+                         const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2) {
   char* p = reinterpret_cast<char*>(body);
   ShapeAcc acc;
   acc.volume = reinterpret_cast<uint32_t*>(p);
@@ -258,21 +348,15 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
   acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
   cudaError_t e = cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
   if (e != cudaSuccess) return e;
-  if (d.nx % 4 == 0) {
-    // 64 threads (256 voxels) per row, 4 rows per CTA
-    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
-    TraceScope t("shape_reduce", s);
+  if (min_lt2 > 1) {  // (every object voxel has LT2 >= 1: thresholds 0 and 1 filter nothing)
     if (d.ndim == 3)
-      shape_reduce4_kernel<3><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+      launch_reduce<3, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, s);
     else
-      shape_reduce4_kernel<2><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+      launch_reduce<2, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, s);
+  } else if (d.ndim == 3) {
+    launch_reduce<3, false>(labels, lt2, n_labels, d, acc, hdr, 0u, s);
   } else {
-    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
-    TraceScope t("shape_reduce", s);
-    if (d.ndim == 3)
-      shape_reduce_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
-    else
-      shape_reduce_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr);
+    launch_reduce<2, false>(labels, lt2, n_labels, d, acc, hdr, 0u, s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
