@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-sphericity evaluation")
     p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--protocol", choices=["object-count"], default=None,
+                   help="run a timing protocol instead of the bench line (prints its own JSON)")
+    p.add_argument("--draws", type=int, default=40, help="object-count protocol: selections per count")
     p.add_argument("--learned-1024", action="store_true",
                    help="also evaluate the learned correction on the 1024^3 volume (slow)")
     return p.parse_args()
@@ -300,6 +303,86 @@ def learned_eval(lt, args, dev):
     return res
 
 
+def object_count_protocol(lt, args, dev):
+    """The paper's second speed protocol (Sec. 5.3) on the synthetic
+    particles: 10 object counts log-spaced in [1, 2000]; for each, `draws`
+    random selections without replacement; for each selection the mean time
+    (CUDA events, ms) to measure the selected objects
+      whole_volume: one lt_measure over the volume holding only them (the
+                    paper's all-objects-at-once use),
+      graph:        one graph launch over per-object crops (lt_batch),
+      per_object:   the same crops launched object after object.
+    Crops are the objects' bounding boxes (outside the array is background,
+    so no margin is needed; particles keep a one-voxel gap, so a crop gives
+    the same DT, LT, S and R as the whole volume: `identical` checks it)."""
+    import torch
+    import scipy.ndimage as ndi
+    import synth
+    mask, labels, n = synth.workload(args.workload, args.seed)
+    boxes = ndi.find_objects(labels.astype(np.int64))
+    objs = []
+    for l, sl in enumerate(boxes, start=1):
+        if sl is None:
+            continue
+        lab = (labels[sl] == l)
+        objs.append({"mask": torch.from_numpy(lab.astype(np.uint8)).to(dev),
+                     "labels": torch.from_numpy(lab.astype(np.int32)).to(dev),
+                     "dt2": torch.empty(lab.shape, dtype=torch.int32, device=dev),
+                     "lt2": torch.empty(lab.shape, dtype=torch.int32, device=dev),
+                     "sphericity": torch.empty(2, dtype=torch.float32, device=dev),
+                     "roundness": torch.empty(2, dtype=torch.float32, device=dev),
+                     "n_labels": 2, "label": l})
+    lab_d = torch.from_numpy(labels.view(np.int32)).to(dev)
+    shape = labels.shape
+    dt2 = torch.empty(shape, dtype=torch.int32, device=dev)
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n, dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    nz, ny, nx = shape
+    ws = lt.workspace(lt.lib.lt_measure_workspace_size(n, 3, nx, ny, nz), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    counts = sorted(set(int(round(c)) for c in np.logspace(0, np.log10(2000), 10)))
+    rng = np.random.default_rng(args.seed)
+    rows = []
+    for k in counts:
+        t_whole, t_graph, t_each, same = [], [], [], True
+        for _ in range(args.draws):
+            pick = rng.choice(len(objs), size=min(k, len(objs)), replace=False)
+            sel = [objs[i] for i in pick]
+            keep = torch.isin(lab_d, torch.tensor([o["label"] for o in sel], dtype=torch.int32, device=dev))
+            m_sel = keep.to(torch.uint8)
+            l_sel = torch.where(keep, lab_d, torch.zeros_like(lab_d))
+            t_whole.append(timed(lambda: lt.lt_measure(m_sel, l_sel, n, dt2, lt2, S, R, ws=ws)))
+            b = lt.Batch(sel, branches=8)
+            t_graph.append(timed(b.run))
+            t_each.append(timed(b.run_eager))
+            b.status()
+            got = torch.stack([torch.stack([o["sphericity"][1], o["roundness"][1]]) for o in sel]).cpu()
+            idx = torch.tensor([o["label"] for o in sel], dtype=torch.long, device=dev)
+            want = torch.stack([S[idx], R[idx]], 1).cpu()
+            same = same and torch.equal(got, want)
+            b.close()
+            del keep, m_sel, l_sel
+        rows.append({"objects": k, "whole_volume_ms": float(np.mean(t_whole)),
+                     "graph_ms": float(np.mean(t_graph)), "per_object_ms": float(np.mean(t_each)),
+                     "identical": bool(same)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"protocol": "object-count", "workload": args.workload, "objects_available": len(objs),
+            "draws": args.draws, "volume": list(shape), "rows": rows}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -354,6 +437,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.protocol == "object-count":
+        if rank == 0:
+            print(json.dumps(object_count_protocol(lt, args, torch.device("cuda", local))), flush=True)
+        return
     mask, labels, n_labels = synth.workload(args.workload, args.seed + rank)
     nd = mask.ndim
     shape = mask.shape
