@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-sphericity evaluation")
     p.add_argument("--batch-steps", type=int, default=10)
-    p.add_argument("--protocol", choices=["object-count"], default=None,
+    p.add_argument("--protocol", choices=["object-count", "scaled-lt"], default=None,
                    help="run a timing protocol instead of the bench line (prints its own JSON)")
     p.add_argument("--draws", type=int, default=40, help="object-count protocol: selections per count")
     p.add_argument("--learned-1024", action="store_true",
@@ -383,6 +383,69 @@ def object_count_protocol(lt, args, dev):
             "draws": args.draws, "volume": list(shape), "rows": rows}
 
 
+def scaled_lt_protocol(lt, args, dev):
+    """Accuracy against speed of the scaled local thickness (LT at 1/s
+    resolution, upsampled; the fast-LT scale option) on the bench workload:
+    per scale s, the time of lt_local_thickness_scaled + lt_shape_measures
+    (full resolution) against the exact lt_measure, and the errors of S, R
+    and LT against the exact values (objects with both finite)."""
+    import torch
+    import synth
+    mask, labels, n = synth.workload(args.workload, args.seed)
+    shape = labels.shape
+    nd = labels.ndim
+    nz, ny, nx = (1,) + shape if nd == 2 else shape
+    m = torch.from_numpy(mask).to(dev)
+    l = torch.from_numpy(labels.view(np.int32)).to(dev)
+    dt2 = torch.empty(shape, dtype=torch.int32, device=dev)
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n, dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    ws = lt.workspace(lt.lib.lt_measure_workspace_size(n, nd, nx, ny, nz), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_exact = timed(lambda: lt.lt_measure(m, l, n, dt2, lt2, S, R, ws=ws))
+    lt.lt_workspace_status(ws)
+    S0, R0, lt_exact = S.cpu().numpy().astype(np.float64), R.cpu().numpy().astype(np.float64), lt2.clone()
+    obj = l != 0
+    rows = [{"scale": 1, "ms": ms_exact, "speedup": 1.0}]
+    for sc in (2, 3, 4):
+        l2s = torch.empty_like(dt2)
+        Ss, Rs = torch.empty_like(S), torch.empty_like(R)
+        sws = lt.workspace(lt.lib.lt_local_thickness_scaled_workspace_size(sc, nd, nx, ny, nz), dev)
+        shws = lt.workspace(lt.lib.lt_shape_workspace_size(n), dev)
+
+        def step():
+            lt.lt_local_thickness_scaled(m, l, sc, l2s, ws=sws)
+            lt.lt_shape_measures(l, l2s, n, Ss, Rs, ws=shws)
+
+        ms = timed(step)
+        lt.lt_workspace_status(sws)
+        a, b = Ss.cpu().numpy().astype(np.float64), Rs.cpu().numpy().astype(np.float64)
+        ok = np.isfinite(a) & np.isfinite(S0)
+        dS, dR = np.abs(a[ok] - S0[ok]), np.abs(b[ok] - R0[ok])
+        dlt = (l2s[obj].double().sqrt() - lt_exact[obj].double().sqrt()).abs()
+        rows.append({"scale": sc, "ms": ms, "speedup": ms_exact / ms,
+                     "S_mae": float(dS.mean()), "S_p95": float(np.quantile(dS, 0.95)), "S_max": float(dS.max()),
+                     "R_mae": float(dR.mean()), "R_p95": float(np.quantile(dR, 0.95)), "R_max": float(dR.max()),
+                     "LT_mae_vox": float(dlt.mean()), "LT_rel_mae": float((dlt / lt_exact[obj].double().sqrt()).mean())})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del sws, shws
+    return {"protocol": "scaled-lt", "workload": args.workload, "objects": n - 1, "rows": rows}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -437,9 +500,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    if args.protocol == "object-count":
+    if args.protocol is not None:
+        fn = {"object-count": object_count_protocol, "scaled-lt": scaled_lt_protocol}[args.protocol]
         if rank == 0:
-            print(json.dumps(object_count_protocol(lt, args, torch.device("cuda", local))), flush=True)
+            print(json.dumps(fn(lt, args, torch.device("cuda", local))), flush=True)
         return
     mask, labels, n_labels = synth.workload(args.workload, args.seed + rank)
     nd = mask.ndim

@@ -126,6 +126,27 @@ lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32
                              int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
                              void* stream);
 
+/* ------------------------------------------------ scaled local thickness --
+ * Approximate LT2 at 1/scale resolution: the reduced-resolution option of
+ * the fast local-thickness work the paper builds on (Sec. 1, Sec. 4),
+ * trading accuracy for speed. From `mask` and `labels` (full resolution):
+ *   sample   low-res voxel B (ceil(n/scale) per axis) takes mask and label of
+ *            the full-res voxel min(scale*B + scale/2, n-1) per axis;
+ *   exact    DT2 and LT2 of the low-res volume (as lt_edt and
+ *            lt_local_thickness compute them);
+ *   upsample object voxel x of label l, block B = x / scale:
+ *            scale^2 * LT2_low(B) when B has label l, else the largest
+ *            scale^2 * LT2_low over the blocks B + d (|d|_inf <= 1) with
+ *            label l, else 1; 0 outside every object.
+ * into `lt2` (full resolution, usable by lt_shape_measures). scale 1 gives
+ * the exact LT2. 1 <= scale <= 8. Device-detected error:
+ * LT_ERR_LABEL_OUTSIDE_MASK. Workspace: lt_local_thickness_scaled_workspace_size
+ * bytes (about 29/scale^ndim bytes per voxel). */
+size_t lt_local_thickness_scaled_workspace_size(int scale, int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_local_thickness_scaled(const uint8_t* mask, const uint32_t* labels, int scale, uint32_t* lt2,
+                                    int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                                    void* stream);
+
 /* --------------------------------------------------------- shape measures --
  * Per-object sphericity and roundness from `labels` and `lt2` (as produced by
  * lt_local_thickness) for labels 0 .. n_labels-1.

@@ -37,6 +37,8 @@ SIGNATURES = {
     "lt_edt": (_i32, [_vp, _vp] + _DIMS + [_vp, _sz, _vp]),
     "lt_local_thickness_workspace_size": (_sz, _DIMS),
     "lt_local_thickness": (_i32, [_vp, _vp, _vp] + _DIMS + [_vp, _sz, _vp]),
+    "lt_local_thickness_scaled_workspace_size": (_sz, [_i32] + _DIMS),
+    "lt_local_thickness_scaled": (_i32, [_vp, _vp, _i32, _vp] + _DIMS + [_vp, _sz, _vp]),
     "lt_shape_workspace_size": (_sz, [_u32]),
     "lt_shape_measures": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp]),
     "lt_shape_measures_filtered": (_i32, [_vp, _vp, _u32, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp]),
@@ -152,6 +154,16 @@ def lt_local_thickness(dt2, labels, lt2, ws=None, stream=None):
         ws = workspace(lib.lt_local_thickness_workspace_size(nd, nx, ny, nz), dt2.device)
     _check(lib.lt_local_thickness(_ptr(dt2), _ptr(labels), _ptr(lt2), nd, nx, ny, nz, _ptr(ws),
                                   ws.numel(), _stream(stream)), "lt_local_thickness")
+    return ws
+
+
+def lt_local_thickness_scaled(mask, labels, scale, lt2, ws=None, stream=None):
+    """Approximate LT2 computed at 1/scale resolution (see include/lt.h)."""
+    nd, nx, ny, nz = _dims(mask)
+    if ws is None:
+        ws = workspace(lib.lt_local_thickness_scaled_workspace_size(scale, nd, nx, ny, nz), mask.device)
+    _check(lib.lt_local_thickness_scaled(_ptr(mask), _ptr(labels), int(scale), _ptr(lt2), nd, nx, ny, nz,
+                                         _ptr(ws), ws.numel(), _stream(stream)), "lt_local_thickness_scaled")
     return ws
 
 

@@ -178,6 +178,31 @@ lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32
   return cuda_status(e);
 }
 
+static constexpr int kMaxScale = 8;
+
+size_t lt_local_thickness_scaled_workspace_size(int scale, int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (scale < 1 || scale > kMaxScale || make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  return sizeof(WsHeader) + scaled_body_bytes(d, scale);
+}
+
+lt_status lt_local_thickness_scaled(const uint8_t* mask, const uint32_t* labels, int scale, uint32_t* lt2,
+                                    int ndim, int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if (scale < 1 || scale > kMaxScale) return LT_ERR_INVALID_ARG;
+  if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK)
+    return st;
+  if ((st = check_ws(ws, ws_bytes, sizeof(WsHeader) + scaled_body_bytes(d, scale))) != LT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = scaled_launch(mask, labels, d, scale, hdr, hdr + 1, lt2, s);
+  return cuda_status(e);
+}
+
 size_t lt_shape_workspace_size(uint32_t n_labels) {
   return sizeof(WsHeader) + shape_workspace_bytes(n_labels);
 }

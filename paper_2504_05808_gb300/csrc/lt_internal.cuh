@@ -80,6 +80,11 @@ cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);
 cudaError_t lt_prepare_device();
 // shape.cu
 size_t shape_workspace_bytes(uint32_t n_labels);
+// scaled.cu: local thickness at 1/s resolution, upsampled (header shared with the low-res pass)
+Dims scaled_dims(const Dims& d, int s);
+size_t scaled_body_bytes(const Dims& d, int s);
+cudaError_t scaled_launch(const uint8_t* mask, const uint32_t* labels, const Dims& d, int s, WsHeader* hdr,
+                          void* body, uint32_t* lt2, cudaStream_t st);
 // roundness mapped to 0-1; r_min < 0: the smallest finite value (scratch: 4 bytes)
 cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* scratch, float* out,
                            cudaStream_t s);
