@@ -742,6 +742,66 @@ __device__ __forceinline__ int owner_lane(int start, int k) {
   return j;
 }
 
+// One 3D row-mode centre, one warp: the lanes take 32 rows (dz, dy) of the
+// ball at a time and compute each row's crescent spans (the row of the ball
+// minus the dominant neighbour's row, clamped to the array); then the spans'
+// voxels are shared out in order, so consecutive lanes update consecutive x.
+__device__ __forceinline__ void paint_centre_rows(const Centre& c, const Dims& d, size_t sy, size_t sz,
+                                                  bool touch, const uint32_t* __restrict__ dt2,
+                                                  const uint32_t* __restrict__ labels,
+                                                  uint32_t* __restrict__ lt2, uint32_t& nupd) {
+  const int lane = threadIdx.x & 31;
+  const int side = 2 * c.R + 1, nrows = side * side;
+  const int xmin = -c.cx, xmax = d.nx - 1 - c.cx;
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    const int r = r0 + lane;
+    int a1 = 0, n1 = 0, a2 = 0, n2 = 0, w = -1;  // spans [a1, a1 + n1), [a2, a2 + n2) of dx
+    uint32_t rowbase = 0;                        // linear index of (cx, y, z)
+    if (r < nrows) {
+      const int q = r / side;
+      const int dz = q - c.R, dy = r - q * side - c.R;
+      const int z = c.cz + dz, y = c.cy + dy;
+      const int h = (int)c.r2 - dz * dz - dy * dy;
+      if (h >= 0 && z >= 0 && z < d.nz && y >= 0 && y < d.ny) {
+        w = (int)isqrt24((uint32_t)h);
+        int hi1 = w, lo2 = 1, hi2 = 0;
+        if (c.r2d >= 0) {
+          const int hd = c.r2d - (dz - c.ddz) * (dz - c.ddz) - (dy - c.ddy) * (dy - c.ddy);
+          if (hd >= 0) {
+            const int wd = (int)isqrt24((uint32_t)hd);
+            hi1 = min(w, c.ddx - wd - 1);
+            lo2 = max(-w, c.ddx + wd + 1);
+            hi2 = w;
+          }
+        }
+        a1 = max(-w, xmin);
+        n1 = max(0, min(hi1, xmax) - a1 + 1);
+        a2 = max(lo2, xmin);
+        n2 = max(0, min(hi2, xmax) - a2 + 1);
+        if (w * w != h) w = -1;  // only the ends of an exact row can be background
+        rowbase = (uint32_t)((size_t)z * sz + (size_t)y * sy + (size_t)c.cx);
+      }
+    }
+    int total;
+    const int start = warp_starts(n1 + n2, lane, &total);
+    for (int kb = 0; kb < total; kb += 32) {
+      const int k = kb + lane;
+      const int j = owner_lane(start, k);
+      const int o = k - __shfl_sync(kFull, start, j);
+      const int a1j = __shfl_sync(kFull, a1, j), n1j = __shfl_sync(kFull, n1, j);
+      const int a2j = __shfl_sync(kFull, a2, j), wj = __shfl_sync(kFull, w, j);
+      const uint32_t rb = __shfl_sync(kFull, rowbase, j);
+      if (k >= total) continue;
+      const int dx = o < n1j ? a1j + o : a2j + (o - n1j);
+      const uint32_t i = rb + (uint32_t)dx;  // modulo 2^32: the sum is in range
+      if (wj >= 0 && (dx == wj || dx == -wj) && dt2[i] == 0) continue;
+      if (touch && labels[i] != c.label) continue;
+      atomicMax(lt2 + i, c.r2);
+      ++nupd;
+    }
+  }
+}
+
 // Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
 // crescent voxels, two per lane in flight. A warp takes kChunkGrab chunks
 // per counter update (one hot counter serialises its atomics).
@@ -880,8 +940,8 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
         }
       } else {
         Centre c;
-        const int items = make_centre<3>(rec, d, sy, sz, touch, dt2, labels, c);
-        for (int k = lane; k < items; k += 32) paint_row_item<3>(c, k, d, sy, sz, touch, dt2, labels, lt2, nupd);
+        make_centre<3>(rec, d, sy, sz, touch, dt2, labels, c);
+        paint_centre_rows(c, d, sy, sz, touch, dt2, labels, lt2, nupd);
       }
     }
     paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
