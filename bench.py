@@ -41,11 +41,12 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-sphericity evaluation")
     p.add_argument("--batch-steps", type=int, default=10)
-    p.add_argument("--protocol", choices=["object-count", "scaled-lt"], default=None,
+    p.add_argument("--targets", default=None,
+                   help="learned-c4 protocol: targets file of tests/golden/make_strict_targets.py c4")
+    p.add_argument("--epochs", type=int, default=40, help="learned-c4 protocol: training epochs")
+    p.add_argument("--protocol", choices=["object-count", "scaled-lt", "learned-c4"], default=None,
                    help="run a timing protocol instead of the bench line (prints its own JSON)")
     p.add_argument("--draws", type=int, default=40, help="object-count protocol: selections per count")
-    p.add_argument("--learned-1024", action="store_true",
-                   help="also evaluate the learned correction on the 1024^3 volume (slow)")
     return p.parse_args()
 
 
@@ -206,15 +207,47 @@ def measure_batch(lt, args, dev):
     return out
 
 
+GOLDEN_TARGETS = os.path.join(ROOT, "tests", "golden", "strict_sphericity_training.txt")
+
+
+def read_golden_targets(path=GOLDEN_TARGETS):
+    """Strict-sphericity targets written by tests/golden/make_strict_targets.py:
+    {seed: (n_labels, crc32 of the labels, targets with NaN where absent)}."""
+    vols, rows = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            if p[0] == "volume":
+                vols[int(p[1])] = (int(p[2]), int(p[3]))
+            else:
+                rows.append((int(p[0]), int(p[1]), float(p[2])))
+    out = {seed: (n, c, np.full(n, np.nan)) for seed, (n, c) in vols.items()}
+    for seed, l, t in rows:
+        out[seed][2][l] = t
+    return out
+
+
+def labels_crc(lab):
+    import zlib
+    return zlib.crc32(np.ascontiguousarray(lab, np.uint32).tobytes()) & 0xFFFFFFFF
+
+
 def learned_eval(lt, args, dev):
     """Train the correction on particles of 5 volumes on the GPU, report MAE
-    against strict sphericity on a 6th (held out), and per-object costs."""
+    against strict sphericity on a 6th (held out), and per-object costs. The
+    targets are the FP64 oracle's, read from tests/golden (written there by
+    tests/golden/make_strict_targets.py for these seeded volumes)."""
     import torch
     import synth
-    import oracle.learned as L
+    golden = read_golden_targets()
     feats, S_all, T_all, t_feat, n_obj_feat = [], [], [], 0.0, 0
     for seed in range(6):
         m, lab, n = synth.training_particles(160, 100 + seed)
+        gn, gcrc, gT = golden[100 + seed]
+        if gn != n or gcrc != labels_crc(lab):
+            raise RuntimeError("training volume differs from the one the golden targets were written for")
         mt = torch.from_numpy(m).to(dev)
         labt = torch.from_numpy(lab.view(np.int32)).to(dev)
         dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
@@ -236,7 +269,7 @@ def learned_eval(lt, args, dev):
         torch.cuda.synchronize()
         t_feat += e0.elapsed_time(e1)
         n_obj_feat += n - 1
-        T = L.strict_sphericity(lab, n)
+        T = gT
         Sn = S.cpu().numpy()
         ok = np.isfinite(T) & np.isfinite(Sn)
         ok[0] = False
@@ -276,30 +309,6 @@ def learned_eval(lt, args, dev):
     e1.record()
     torch.cuda.synchronize()
     res["infer_ns_per_object"] = e0.elapsed_time(e1) / 5 * 1e6 / big
-    if args.learned_1024:
-        m, lab, n = synth.workload("particles_3d_1024", 0)
-        mt = torch.from_numpy(m).to(dev)
-        labt = torch.from_numpy(lab.view(np.int32)).to(dev)
-        dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
-        lt2 = torch.empty_like(dt2)
-        Sg = torch.empty(n, dtype=torch.float32, device=dev)
-        Rg = torch.empty_like(Sg)
-        stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
-        stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
-        lt.lt_edt(mt, dt2)
-        lt.lt_local_thickness(dt2, labt, lt2)
-        lt.lt_shape_measures(labt, lt2, n, Sg, Rg, stats)
-        Fg = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
-        lt.lt_object_features(labt, lt2, n, stats, Sg, Rg, Fg)
-        og = torch.empty(n, dtype=torch.float32, device=dev)
-        lt.lt_mlp_infer(p, Fg, Sg, og)
-        T = L.strict_sphericity(lab, n)
-        Sn, On = Sg.cpu().numpy(), og.cpu().numpy()
-        ok = np.isfinite(T) & np.isfinite(Sn)
-        ok[0] = False
-        res["volume_1024"] = {"objects": int(ok.sum()),
-                              "mae_plain": float(np.abs(Sn[ok] - T[ok]).mean()),
-                              "mae_learned": float(np.abs(On[ok] - T[ok]).mean())}
     return res
 
 
@@ -446,6 +455,108 @@ def scaled_lt_protocol(lt, args, dev):
     return {"protocol": "scaled-lt", "workload": args.workload, "objects": n - 1, "rows": rows}
 
 
+def _object_features(lt, dev, m, lab, n):
+    """GPU pipeline + features of one volume: (S, R, features) as numpy and the
+    device times (ms) of the pipeline and of the features pass."""
+    import torch
+    mt = torch.from_numpy(m).to(dev)
+    labt = torch.from_numpy(lab.view(np.int32)).to(dev)
+    dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n, dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
+    stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
+    F = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    lt.lt_edt(mt, dt2)
+    ws = lt.lt_local_thickness(dt2, labt, lt2)
+    lt.lt_shape_measures(labt, lt2, n, S, R, stats)
+    ev[1].record()
+    lt.lt_object_features(labt, lt2, n, stats, S, R, F)
+    ev[2].record()
+    torch.cuda.synchronize()
+    lt.lt_workspace_status(ws)
+    return (S.cpu().numpy(), R.cpu().numpy(), F.cpu().numpy(), ev[0].elapsed_time(ev[1]),
+            ev[1].elapsed_time(ev[2]))
+
+
+def learned_c4_protocol(lt, args, dev):
+    """The learned-sphericity configuration at scale: train the correction on
+    the GPU on the particles of N volumes of the widened 512^3 mix (~200 k
+    particles for N = 82 at 320^3) and evaluate it on the 1024^3 volume of
+    ~1 M particles: MAE of the plain S_LT and of the learned S against strict
+    sphericity, and per-object costs. Targets (the FP64 oracle's strict
+    sphericity) are read from --targets, written for the same seeded volumes
+    by tests/golden/make_strict_targets.py c4."""
+    import concurrent.futures as cf
+    import torch
+    import synth
+    with np.load(args.targets) as z:  # read everything here: NpzFile is not thread-safe
+        d = {k: z[k] for k in z.files}
+    n_train = int(d["n_train"])
+    feats, S_all, T_all = [], [], []
+
+    def gen(i):
+        crc_, n_, edge = (int(v) for v in d[f"train_{i}_crc"])
+        m, lab, n = synth.training_particles(edge, 1000 + i)
+        if n != n_ or labels_crc(lab) != crc_:
+            raise RuntimeError(f"training volume {i} differs from the one its targets were written for")
+        return m, lab, n, d[f"train_{i}"]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=max(1, (os.cpu_count() or 4) // 2)) as ex:
+        for m, lab, n, T in ex.map(gen, range(n_train)):
+            S, R, F, _, _ = _object_features(lt, dev, m, lab, n)
+            ok = np.isfinite(T) & np.isfinite(S)
+            ok[0] = False
+            feats.append(F[ok])
+            S_all.append(S[ok])
+            T_all.append(T[ok].astype(np.float32))
+    prep_s = time.perf_counter() - t0
+    F = torch.from_numpy(np.concatenate(feats)).to(dev)
+    S = torch.from_numpy(np.concatenate(S_all)).to(dev)
+    T = torch.from_numpy(np.concatenate(T_all)).to(dev)
+    p = torch.from_numpy(synth.mlp_initial_params(0)).to(dev)
+    t0 = time.perf_counter()
+    hist = lt.train_mlp(p, F, S, T, np.arange(len(S)), epochs=args.epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del F, S, T, feats
+    # evaluation on the 1024^3 volume
+    crc_, n_, _ = (int(v) for v in d["eval_crc"])
+    m, lab, n = synth.workload("particles_3d_1024", 0)
+    if n != n_ or labels_crc(lab) != crc_:
+        raise RuntimeError("1024^3 volume differs from the one its targets were written for")
+    Te = d["eval"]
+    Sg, Rg, Fg, ms_pipe, ms_feat = _object_features(lt, dev, m, lab, n)
+    Ft = torch.from_numpy(Fg).to(dev)
+    St = torch.from_numpy(Sg).to(dev)
+    og = torch.empty(n, dtype=torch.float32, device=dev)
+    lt.lt_mlp_infer(p, Ft, St, og)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lt.lt_mlp_infer(p, Ft, St, og)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_inf = e0.elapsed_time(e1)
+    On = og.cpu().numpy()
+    ok = np.isfinite(Te) & np.isfinite(Sg)
+    ok[0] = False
+    n_obj = int(ok.sum())
+    return {"protocol": "learned-c4", "train_volumes": n_train, "train_objects": int(sum(len(x) for x in S_all)),
+            "epochs": args.epochs, "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
+            "prep_s": prep_s, "eval_volume": "particles_3d_1024", "eval_objects": n_obj,
+            "mae_plain": float(np.abs(Sg[ok] - Te[ok]).mean()),
+            "mae_learned": float(np.abs(On[ok] - Te[ok]).mean()),
+            "per_object_ns": {"plain_pipeline": ms_pipe * 1e6 / max(1, n - 1),
+                              "features": ms_feat * 1e6 / max(1, n - 1),
+                              "inference": ms_inf * 1e6 / max(1, n - 1)},
+            "target": "strict sphericity, FP64 oracle (smoothed marching tetrahedra), precomputed"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -501,7 +612,8 @@ def main():
             dist.barrier()
 
     if args.protocol is not None:
-        fn = {"object-count": object_count_protocol, "scaled-lt": scaled_lt_protocol}[args.protocol]
+        fn = {"object-count": object_count_protocol, "scaled-lt": scaled_lt_protocol,
+              "learned-c4": learned_c4_protocol}[args.protocol]
         if rank == 0:
             print(json.dumps(fn(lt, args, torch.device("cuda", local))), flush=True)
         return

@@ -1,0 +1,122 @@
+"""Writes strict-sphericity targets for seeded synthetic particle volumes.
+
+The targets of the learned sphericity correction are the FP64 oracle's
+strict sphericity (Eq. 1 on a marching-tetrahedra mesh of the object's
+indicator smoothed by a Gaussian of one voxel; oracle.learned). This script
+is the only place that computes them outside the tests: it calls only
+oracle/ and the seeded generators in synth/, and writes plain numbers that
+bench.py reads, so the measurement never runs the oracle itself.
+
+  python tests/golden/make_strict_targets.py bench
+      the six 160^3 training volumes of bench.py's learned leg
+      -> tests/golden/strict_sphericity_training.txt
+  python tests/golden/make_strict_targets.py c4 --out FILE.npz [--train-volumes N] [--edge E]
+      N training volumes of edge E (about 2,440 particles each at E = 320;
+      82 volumes give ~200 k particles) and the 1024^3 volume of ~1 M
+      particles -> FILE.npz (crc32 of each volume's labels, targets with NaN
+      for absent labels)
+
+Each volume is identified by the generator call and the crc32 of its labels,
+which the reader checks before using the targets.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import os
+import sys
+import zlib
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import oracle.learned as L  # noqa: E402
+import synth  # noqa: E402
+
+BENCH_FILE = os.path.join(HERE, "strict_sphericity_training.txt")
+BENCH_EDGE, BENCH_SEEDS = 160, tuple(range(100, 106))
+
+
+def crc(labels: np.ndarray) -> int:
+    return zlib.crc32(np.ascontiguousarray(labels, np.uint32).tobytes()) & 0xFFFFFFFF
+
+
+def targets(labels: np.ndarray, n: int) -> np.ndarray:
+    return L.strict_sphericity(labels, n)
+
+
+def write_bench() -> None:
+    lines = ["# strict sphericity (FP64 oracle: smoothed marching-tetrahedra mesh, Eq. 1)",
+             f"# of synth.training_particles({BENCH_EDGE}, seed); written by make_strict_targets.py",
+             "# 'volume seed n_labels crc32' then 'seed label target' for every finite target"]
+    body = []
+    for seed in BENCH_SEEDS:
+        _, lab, n = synth.training_particles(BENCH_EDGE, seed)
+        T = targets(lab, n)
+        lines.append(f"volume {seed} {n} {crc(lab)}")
+        body += [f"{seed} {l} {T[l]:.17g}" for l in range(1, n) if np.isfinite(T[l])]
+    with open(BENCH_FILE, "w") as f:
+        f.write("\n".join(lines + body) + "\n")
+
+
+def read_bench(path: str = BENCH_FILE):
+    """{seed: (n_labels, crc32, targets[n_labels] with NaN where absent)}"""
+    vols, rows = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            if p[0] == "volume":
+                vols[int(p[1])] = (int(p[2]), int(p[3]))
+            else:
+                rows.append((int(p[0]), int(p[1]), float(p[2])))
+    out = {}
+    for seed, (n, c) in vols.items():
+        T = np.full(n, np.nan)
+        out[seed] = (n, c, T)
+    for seed, l, t in rows:
+        out[seed][2][l] = t
+    return out
+
+
+def write_c4(path: str, n_train: int, edge: int, threads: int) -> None:
+    res = {}
+
+    def one(i):
+        _, lab, n = synth.training_particles(edge, 1000 + i)
+        return i, n, crc(lab), lab
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for i, n, c, lab in ex.map(one, range(n_train)):
+            res[f"train_{i}_crc"] = np.array([c, n, edge], np.int64)
+            res[f"train_{i}"] = targets(lab, n)
+            del lab
+            print(f"train volume {i}: {n - 1} labels", file=sys.stderr, flush=True)
+    _, lab, n = synth.workload("particles_3d_1024", 0)
+    res["eval_crc"] = np.array([crc(lab), n, 1024], np.int64)
+    res["eval"] = targets(lab, n)
+    np.savez(path, n_train=np.array(n_train), **res)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("set", choices=["bench", "c4"])
+    p.add_argument("--out")
+    p.add_argument("--train-volumes", type=int, default=82)
+    p.add_argument("--edge", type=int, default=320)
+    p.add_argument("--threads", type=int, default=os.cpu_count() or 4)
+    a = p.parse_args()
+    oracle.build()
+    if a.set == "bench":
+        write_bench()
+    else:
+        write_c4(a.out, a.train_volumes, a.edge, a.threads)
+
+
+if __name__ == "__main__":
+    main()
