@@ -64,6 +64,111 @@ __global__ void __launch_bounds__(256) features_hist_kernel(const uint32_t* __re
   if (key != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(hist + key, (uint32_t)__popc(peers));
 }
 
+// Bin of LT2 t in an object with largest LT2 mx (t <= mx): the largest b in
+// 0..15 with b^2 mx <= 256 t, from a float estimate fixed in integers.
+__device__ __forceinline__ uint32_t lt_bin(uint32_t t, uint32_t mx) {
+  int b = min(15, (int)(16.0f * sqrtf((float)t / (float)max(mx, 1u))));
+  const unsigned long long T = 256ull * t, M = mx;
+  while (b < 15 && (unsigned long long)((b + 1) * (b + 1)) * M <= T) ++b;
+  while (b > 0 && (unsigned long long)(b * b) * M > T) --b;
+  return (uint32_t)b;
+}
+
+// Vector form for nx % 4 == 0: a thread bins 4 consecutive voxels of a row
+// (16-byte loads of labels, LT2 and the neighbouring rows); equal keys
+// (label, shell, bin) of consecutive voxels are counted together, and runs of
+// equal first keys across the warp are combined by a segmented scan so that
+// one lane per run issues the atomic.
+__device__ __forceinline__ uint32_t c4(const uint4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(256) features_hist4_kernel(const uint32_t* __restrict__ labels,
+                                                             const uint32_t* __restrict__ lt2, Dims d,
+                                                             uint32_t n_labels,
+                                                             const uint32_t* __restrict__ max_lt2,
+                                                             uint32_t* __restrict__ hist) {
+  const int lane = threadIdx.x & 31;
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const bool in = x0 < d.nx && y < d.ny;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x0 : 0;
+  uint4 L = make_uint4(0u, 0u, 0u, 0u);
+  if (in) L = *reinterpret_cast<const uint4*>(labels + v);
+  const bool any = (L.x | L.y | L.z | L.w) != 0u;
+  if (__ballot_sync(0xffffffffu, any) == 0) return;  // uniform per warp
+  uint32_t key = 0xffffffffu, cnt = 0;  // this thread's first key and its count
+  if (any) {
+    const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
+    const uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
+    uint4 Zm = zero, Zp = zero;
+    if (NDIM == 3) {
+      if (z > 0) Zm = *reinterpret_cast<const uint4*>(labels + v - sz);
+      if (z + 1 < d.nz) Zp = *reinterpret_cast<const uint4*>(labels + v + sz);
+    }
+    const uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
+    const uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
+    uint32_t prev = 0xffffffffu, run = 0, lm = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t l = c4(L, k);
+      uint32_t kk = 0xffffffffu;
+      if (l != 0 && l < n_labels) {
+        const uint32_t left = k == 0 ? xl : c4(L, k - 1), right = k == 3 ? xr : c4(L, k + 1);
+        bool s = left != l || right != l || c4(Ym, k) != l || c4(Yp, k) != l;
+        if (NDIM == 3) s = s || c4(Zm, k) != l || c4(Zp, k) != l;
+        if (l != lm) {
+          lm = l;
+          mx = max_lt2[l];
+        }
+        kk = l * 32u + (s ? 16u : 0u) + lt_bin(c4(T, k), mx);
+      }
+      if (kk != prev) {  // close the previous run
+        if (prev != 0xffffffffu) {
+          if (key == 0xffffffffu) {
+            key = prev;
+            cnt = run;
+          } else {
+            atomicAdd(hist + prev, run);
+          }
+        }
+        prev = kk;
+        run = 0;
+      }
+      ++run;
+    }
+    if (prev != 0xffffffffu) {
+      if (key == 0xffffffffu) {
+        key = prev;
+        cnt = run;
+      } else if (prev == key) {
+        cnt += run;
+      } else {
+        atomicAdd(hist + prev, run);
+      }
+    }
+  }
+  // segmented inclusive scan of the counts over runs of equal keys
+  const uint32_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  int seg = (lane == 0 || kprev != key) ? lane : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, seg, o);
+    if (lane >= o) seg = max(seg, t);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, cnt, o);
+    if (lane - o >= seg) cnt += a;
+  }
+  const uint32_t knext = __shfl_down_sync(0xffffffffu, key, 1);
+  if (key != 0xffffffffu && (lane == 31 || knext != key)) atomicAdd(hist + key, cnt);
+}
+
 __global__ void features_final_kernel(uint32_t n_labels, lt_object_stats st, const float* __restrict__ S,
                                       const float* __restrict__ R, const uint32_t* __restrict__ hist,
                                       float* __restrict__ F) {
@@ -260,13 +365,22 @@ cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_
   uint32_t* hist = reinterpret_cast<uint32_t*>(body);
   cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)n_labels * 32 * 4, s);
   if (e != cudaSuccess) return e;
-  dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
   {
     TraceScope t("features_hist", s);
-    if (d.ndim == 3)
-      features_hist_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
-    else
-      features_hist_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
+    if (d.nx % 4 == 0) {
+      // 64 threads (256 voxels) per row, 4 rows per CTA
+      dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+      if (d.ndim == 3)
+        features_hist4_kernel<3><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
+      else
+        features_hist4_kernel<2><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
+    } else {
+      dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
+      if (d.ndim == 3)
+        features_hist_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
+      else
+        features_hist_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
