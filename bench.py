@@ -122,9 +122,11 @@ def algorithmic_bytes(name, n, n_surv):
     return table.get(name)
 
 
-# DRAM bytes (read + write) per launch from an ncu capture of the same kernel
-# source on the same workload; None until captured for the current kernels.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read
+# and _write, one pass) of the current kernels on the 512^3 particle volume;
+# valid for that workload only.
+TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344350000, "edt_cols_y": 751950000, "edt_cols_z": 1015030000,
+                                "lt_ridge": 1768680000, "lt_paint": 1567780000, "shape_reduce": 848664220}}
 
 
 def update_rate_probe(lt, dev):
@@ -698,6 +700,9 @@ def main():
         if ab is not None:
             e.update({"algorithmic_bytes": ab, "achieved_gbs": ab / (avg * 1e-3) / 1e9})
             e["frac_hbm"] = e["achieved_gbs"] / peak
+        tr = TRAFFIC.get(args.workload, {}).get(k)
+        if tr is not None:
+            e["traffic"] = tr
         if k == "lt_paint":
             e.update({"updates": counters["updates"],
                       "achieved_gupd": counters["updates"] / (avg * 1e-3) / 1e9})
@@ -708,12 +713,12 @@ def main():
         upeak = max(probe.values())
         roof = {"kernel": dom, "bound": "atomic", "achieved": kd["achieved_gupd"], "peak": upeak,
                 "unit": "Gupdates/s", "frac": kd["achieved_gupd"] / upeak,
-                "traffic": TRAFFIC.get(dom), "avg_ms": kd["avg_ms"], "updates": counters["updates"],
+                "traffic": TRAFFIC.get(args.workload, {}).get(dom), "avg_ms": kd["avg_ms"], "updates": counters["updates"],
                 "peak_source": "measured in this run by lt_probe_update_rate (best of its patterns)",
                 "probe_gupd": probe}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": kd.get("achieved_gbs"), "peak": peak,
-                "unit": "GB/s", "frac": kd.get("frac_hbm"), "traffic": TRAFFIC.get(dom),
+                "unit": "GB/s", "frac": kd.get("frac_hbm"), "traffic": TRAFFIC.get(args.workload, {}).get(dom),
                 "avg_ms": kd["avg_ms"], "algorithmic_bytes": kd.get("algorithmic_bytes"),
                 "peak_source": peak_kind}
     gpu_launches = sum(v[0] for v in trace.values())
