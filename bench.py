@@ -44,7 +44,8 @@ def parse():
     p.add_argument("--targets", default=None,
                    help="learned-c4 protocol: targets file of tests/golden/make_strict_targets.py c4")
     p.add_argument("--epochs", type=int, default=40, help="learned-c4 protocol: training epochs")
-    p.add_argument("--protocol", choices=["object-count", "scaled-lt", "learned-c4"], default=None,
+    p.add_argument("--planes", type=int, default=64, help="slabs protocol: z planes per slab")
+    p.add_argument("--protocol", choices=["object-count", "scaled-lt", "learned-c4", "slabs"], default=None,
                    help="run a timing protocol instead of the bench line (prints its own JSON)")
     p.add_argument("--draws", type=int, default=40, help="object-count protocol: selections per count")
     return p.parse_args()
@@ -559,6 +560,43 @@ def learned_c4_protocol(lt, args, dev):
             "target": "strict sphericity, FP64 oracle (smoothed marching tetrahedra), precomputed"}
 
 
+def slabs_protocol(lt, args, dev):
+    """The slab form (host-resident volume, --planes z planes on the device at
+    a time) against the in-core host-buffer entry point on the same pinned
+    host buffers: device memory used, Mvoxels/s end to end, identical S, R."""
+    import torch
+    import synth
+    mask, labels, n = synth.workload(args.workload, args.seed)
+    nz, ny, nx = mask.shape
+    mh = torch.from_numpy(mask).pin_memory()
+    lh = torch.from_numpy(labels.view(np.int32)).pin_memory()
+    dt2 = torch.empty(mask.shape, dtype=torch.int32).pin_memory()
+    S1, R1 = torch.empty(n).pin_memory(), torch.empty(n).pin_memory()
+    S2, R2 = torch.empty(n).pin_memory(), torch.empty(n).pin_memory()
+    wss = lt.workspace(lt.lib.lt_measure_slabs_workspace_size(n, nx, ny, nz, args.planes), dev)
+    lt.lt_measure_slabs(mh, lh, n, args.planes, dt2, None, S1, R1, ws=wss)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lt.lt_measure_slabs(mh, lh, n, args.planes, dt2, None, S1, R1, ws=wss)
+    t_slabs = (time.perf_counter() - t0) / 3
+    slab_bytes = wss.numel()
+    del wss
+    torch.cuda.empty_cache()
+    wsh = lt.workspace(lt.lt_measure_host_workspace_size(n, mask.shape), dev)
+    lt.lt_measure_host(mh, lh, n, S2, R2, wsh)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lt.lt_measure_host(mh, lh, n, S2, R2, wsh)
+    t_core = (time.perf_counter() - t0) / 3
+    same = bool(np.array_equal(S1.numpy(), S2.numpy(), equal_nan=True) and
+                np.array_equal(R1.numpy(), R2.numpy(), equal_nan=True))
+    return {"protocol": "slabs", "workload": args.workload, "planes": args.planes,
+            "device_bytes_slabs": int(slab_bytes), "device_bytes_in_core": int(wsh.numel()),
+            "slabs_ms": t_slabs * 1e3, "in_core_ms": t_core * 1e3,
+            "slabs_mvox_s": mask.size / t_slabs / 1e6, "in_core_mvox_s": mask.size / t_core / 1e6,
+            "identical": same}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -615,7 +653,7 @@ def main():
 
     if args.protocol is not None:
         fn = {"object-count": object_count_protocol, "scaled-lt": scaled_lt_protocol,
-              "learned-c4": learned_c4_protocol}[args.protocol]
+              "learned-c4": learned_c4_protocol, "slabs": slabs_protocol}[args.protocol]
         if rank == 0:
             print(json.dumps(fn(lt, args, torch.device("cuda", local))), flush=True)
         return

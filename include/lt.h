@@ -321,6 +321,28 @@ lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_lab
                      int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2,
                      uint32_t* lt2, float* sphericity, float* roundness, void* stream);
 
+/* Slab form of lt_measure for volumes held in host memory whose working set
+ * does not fit the device (or a budget on it): the device works on
+ * `slab_planes` z planes at a time (workspace ~28 bytes per voxel of a slab,
+ * lt_measure_slabs_workspace_size). Results equal lt_measure's bit for bit.
+ * Phases: x/y EDT passes per slab (the y pass's output goes to dt2_host);
+ * the z pass per band of rows over all z (2D copies, in place in dt2_host,
+ * which then holds DT2); local thickness and the shape sums per core slab,
+ * uploaded with H + 1 planes on each side, H = ceil(sqrt(max DT2)) (a ball
+ * holding a core voxel has its centre within H planes); the formulas once.
+ * 3D only. Host buffers: mask_host, labels_host (inputs, n voxels),
+ * dt2_host (n uint32, required: scratch, then DT2), lt2_host (n uint32 or
+ * NULL), sphericity_host and roundness_host (n_labels floats); pinned memory
+ * copies fastest. Axes up to 8192, the smallest at most 8190 (DT2 < 2^24);
+ * n itself may exceed 2^32; slab_planes * nx * ny < 2^32. Waits for the
+ * stream. LT_ERR_WORKSPACE also when the objects are too thick for the slab
+ * (2 H + 3 > slab_planes): use more planes. */
+size_t lt_measure_slabs_workspace_size(uint32_t n_labels, int64_t nx, int64_t ny, int64_t nz, int slab_planes);
+lt_status lt_measure_slabs(const uint8_t* mask_host, const uint32_t* labels_host, uint32_t n_labels, int64_t nx,
+                           int64_t ny, int64_t nz, int slab_planes, uint32_t* dt2_host, uint32_t* lt2_host,
+                           float* sphericity_host, float* roundness_host, void* ws, size_t ws_bytes,
+                           void* stream);
+
 /* Host-buffer form of lt_measure for callers whose data lives in host memory:
  * copies mask_host and labels_host to the device, runs the pipeline, copies
  * sphericity_host and roundness_host (n_labels floats each) back and waits

@@ -46,6 +46,8 @@ SIGNATURES = {
     "lt_roundness_rescale": (_i32, [_vp, _u32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "lt_measure_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "lt_measure_slabs_workspace_size": (_sz, [_u32, _i64, _i64, _i64, _i32]),
+    "lt_measure_slabs": (_i32, [_vp, _vp, _u32, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure_host": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp]),
     "lt_workspace_status": (_i32, [_vp, _sz, _vp]),
@@ -233,6 +235,23 @@ def lt_measure_host(mask_host, labels_host, n_labels, sphericity_host, roundness
                                _ptr(ws), ws.numel(), ctypes.c_void_p(sphericity_host.data_ptr()),
                                ctypes.c_void_p(roundness_host.data_ptr()), _stream(stream)),
            "lt_measure_host")
+
+
+def lt_measure_slabs(mask_host, labels_host, n_labels, slab_planes, dt2_host, lt2_host, sphericity_host,
+                     roundness_host, ws=None, device="cuda", stream=None):
+    """Slab form of lt_measure over host tensors (3D; see include/lt.h);
+    lt2_host may be None. Waits for the stream; returns the workspace."""
+    nz, ny, nx = mask_host.shape
+    for t in (mask_host, labels_host, dt2_host, sphericity_host, roundness_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected contiguous host tensors")
+    if ws is None:
+        ws = workspace(lib.lt_measure_slabs_workspace_size(n_labels, nx, ny, nz, slab_planes), device)
+    hp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(lib.lt_measure_slabs(hp(mask_host), hp(labels_host), n_labels, nx, ny, nz, int(slab_planes),
+                                hp(dt2_host), hp(lt2_host), hp(sphericity_host), hp(roundness_host), _ptr(ws),
+                                ws.numel(), _stream(stream)), "lt_measure_slabs")
+    return ws
 
 
 def lt_measure_host_workspace_size(n_labels, shape):

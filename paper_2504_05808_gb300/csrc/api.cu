@@ -324,6 +324,37 @@ lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
   return LT_OK;
 }
 
+static bool slab_dims_ok(int64_t nx, int64_t ny, int64_t nz, int slab_planes) {
+  if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxAxis || ny > kMaxAxis || nz > kMaxAxis) return false;
+  const int64_t mn = std::min(nx, std::min(ny, nz));
+  if ((mn + 1) / 2 * ((mn + 1) / 2) >= (1 << 24)) return false;  // DT2 < 2^24
+  return slab_planes >= 1 && (uint64_t)slab_planes * (uint64_t)(nx * ny) < (1ull << 32);
+}
+
+size_t lt_measure_slabs_workspace_size(uint32_t n_labels, int64_t nx, int64_t ny, int64_t nz, int slab_planes) {
+  if (n_labels == 0 || !slab_dims_ok(nx, ny, nz, slab_planes)) return 0;
+  return slabs_ws_bytes(n_labels, (int)nx, (int)ny, slab_planes);
+}
+
+lt_status lt_measure_slabs(const uint8_t* mask_host, const uint32_t* labels_host, uint32_t n_labels, int64_t nx,
+                           int64_t ny, int64_t nz, int slab_planes, uint32_t* dt2_host, uint32_t* lt2_host,
+                           float* sphericity_host, float* roundness_host, void* ws, size_t ws_bytes,
+                           void* stream) {
+  if (!mask_host || !labels_host || !dt2_host || !sphericity_host || !roundness_host || n_labels == 0)
+    return LT_ERR_INVALID_ARG;
+  if (!slab_dims_ok(nx, ny, nz, slab_planes)) return LT_ERR_DIMS;
+  lt_status st = check_ws(ws, ws_bytes, slabs_ws_bytes(n_labels, (int)nx, (int)ny, slab_planes));
+  if (st != LT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  st = slabs_run(mask_host, labels_host, n_labels, (int)nx, (int)ny, (int)nz, slab_planes, dt2_host, lt2_host,
+                 sphericity_host, roundness_host, ws, ws_bytes, s);
+  if (st != LT_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  return lt_workspace_status(ws, ws_bytes, stream);
+}
+
 size_t lt_roundness_rescale_workspace_size(void) { return kAlign; }
 
 lt_status lt_roundness_rescale(const float* roundness, uint32_t n, float r_min, float* out, void* ws,

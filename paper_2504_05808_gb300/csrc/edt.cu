@@ -303,9 +303,15 @@ size_t edt_workspace_bytes(const Dims& d) {
 }
 
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* ws, cudaStream_t s,
-                       const Tuning& tu) {
+                       const Tuning& tu, int passes) {
   uint16_t* g = reinterpret_cast<uint16_t*>(ws);
   uint32_t* tmp = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + align_up((size_t)d.n * sizeof(uint16_t)));
+  const size_t plane = (size_t)d.nx * d.ny;
+  if (!(passes & 1)) {  // z pass only, on the y pass's output already in dt2
+    if (d.ndim == 2) return cudaSuccess;
+    return col_pass<uint32_t>("edt_cols_z", dt2, dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s,
+                              tu.edt_tx_z);
+  }
   const uint32_t nrows = (uint32_t)d.ny * (uint32_t)d.nz;
   const unsigned blocks = (nrows + 7) / 8;
   {
@@ -317,11 +323,10 @@ cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t plane = (size_t)d.nx * d.ny;
   // y: columns of length ny, stride nx; one tile row per z; g -> dt2.
   e = col_pass<uint16_t>("edt_cols_y", g, dt2, d.ny, (size_t)d.nx, d.nx, plane, d.nz, tmp, d.n, s,
                          tu.edt_tx_y);
-  if (e != cudaSuccess || d.ndim == 2) return e;
+  if (e != cudaSuccess || d.ndim == 2 || !(passes & 2)) return e;
   // z: columns of length nz, stride nx*ny; one tile row per y; in place.
   return col_pass<uint32_t>("edt_cols_z", dt2, dt2, d.nz, plane, d.nx, (size_t)d.nx, d.ny, tmp, d.n, s,
                             tu.edt_tx_z);

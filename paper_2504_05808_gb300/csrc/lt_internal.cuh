@@ -27,7 +27,8 @@ struct WsHeader {
   uint32_t ctr_small, ctr_big;  // work counters of the paint kernel
   unsigned long long n_updates;        // LT2 updates (atomic max) the paint kernel issued
   unsigned long long n_table_updates;  // of which from crescent tables
-  uint32_t reserved[54];
+  uint32_t max_dt2;                    // slab pipeline: largest DT2 of the volume
+  uint32_t reserved[53];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -67,8 +68,9 @@ struct Tuning {
 // edt.cu
 size_t edt_workspace_bytes(const Dims& d);
 cudaError_t edt_prepare_device();  // kernel attributes; call before capture
+// passes: 1 = x and y, 2 = z (on dt2 in place), 3 = all
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* ws, cudaStream_t s,
-                       const Tuning& tu = Tuning());
+                       const Tuning& tu = Tuning(), int passes = 3);
 // lt.cu
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
@@ -80,6 +82,11 @@ cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);
 cudaError_t lt_prepare_device();
 // shape.cu
 size_t shape_workspace_bytes(uint32_t n_labels);
+// slabs.cu: the pipeline over a host-resident volume, z-slab by z-slab
+size_t slabs_ws_bytes(uint32_t n_labels, int nx, int ny, int P);
+lt_status slabs_run(const uint8_t* mask_h, const uint32_t* labels_h, uint32_t n_labels, int nx, int ny, int nz,
+                    int P, uint32_t* dt2_h, uint32_t* lt2_h, float* S_h, float* R_h, void* ws, size_t ws_bytes,
+                    cudaStream_t s);
 // scaled.cu: local thickness at 1/s resolution, upsampled (header shared with the low-res pass)
 Dims scaled_dims(const Dims& d, int s);
 size_t scaled_body_bytes(const Dims& d, int s);
@@ -88,6 +95,14 @@ cudaError_t scaled_launch(const uint8_t* mask, const uint32_t* labels, const Dim
 // roundness mapped to 0-1; r_min < 0: the smallest finite value (scratch: 4 bytes)
 cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* scratch, float* out,
                            cudaStream_t s);
+// the shape stage in three steps (shape_launch runs all three): clear the
+// accumulators, add planes [z_lo, z_hi) of a (sub-)volume (the planes
+// around them are read for the shell test), and the formulas
+cudaError_t shape_clear(void* body, uint32_t n_labels, cudaStream_t s);
+cudaError_t shape_accumulate(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                             WsHeader* hdr, void* body, int z_lo, int z_hi, cudaStream_t s, uint32_t min_lt2 = 0);
+cudaError_t shape_finalize(int ndim, uint32_t n_labels, void* body, float* S, float* R,
+                           const lt_object_stats* stats, cudaStream_t s);
 // min_lt2 > 1: the objects are reduced to their voxels with LT2 >= min_lt2
 cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,

@@ -42,10 +42,11 @@ template <int NDIM, bool FILTER>
 __global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __restrict__ labels,
                                                            const uint32_t* __restrict__ lt2, Dims d,
                                                            uint32_t n_labels, ShapeAcc acc,
-                                                           WsHeader* __restrict__ hdr, uint32_t min_lt2) {
+                                                           WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                           int z_lo) {
   const int lane = threadIdx.x & 31;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + z_lo;
   const bool in = x < d.nx;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x : 0;
@@ -122,10 +123,11 @@ template <int NDIM, bool FILTER>
 __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
                                                             const uint32_t* __restrict__ lt2, Dims d,
                                                             uint32_t n_labels, ShapeAcc acc,
-                                                            WsHeader* __restrict__ hdr, uint32_t min_lt2) {
+                                                            WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                            int z_lo) {
   const int lane = threadIdx.x & 31;
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z + z_lo;
   const bool in = x0 < d.nx && y < d.ny;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x0 : 0;
@@ -320,21 +322,19 @@ size_t shape_workspace_bytes(uint32_t n_labels) { return acc_bytes(n_labels); }
 
 template <int NDIM, bool FILTER>
 void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
-                   const ShapeAcc& acc, WsHeader* hdr, uint32_t min_lt2, cudaStream_t s) {
+                   const ShapeAcc& acc, WsHeader* hdr, uint32_t min_lt2, int z_lo, int z_hi, cudaStream_t s) {
   TraceScope t("shape_reduce", s);
   if (d.nx % 4 == 0) {
     // 64 threads (256 voxels) per row, 4 rows per CTA
-    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
-    shape_reduce4_kernel<NDIM, FILTER><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2);
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, z_hi - z_lo);
+    shape_reduce4_kernel<NDIM, FILTER><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo);
   } else {
-    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
-    shape_reduce_kernel<NDIM, FILTER><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2);
+    dim3 grid((d.nx + 255) / 256, d.ny, z_hi - z_lo);
+    shape_reduce_kernel<NDIM, FILTER><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo);
   }
 }
 
-cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
-                         const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
-                         const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2) {
+ShapeAcc acc_layout(void* body, uint32_t n_labels) {
   char* p = reinterpret_cast<char*>(body);
   ShapeAcc acc;
   acc.volume = reinterpret_cast<uint32_t*>(p);
@@ -346,31 +346,53 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
   acc.sum_lt = reinterpret_cast<unsigned long long*>(p);
   p += align_up((size_t)n_labels * 8);
   acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
-  cudaError_t e = cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
-  if (e != cudaSuccess) return e;
+  return acc;
+}
+
+cudaError_t shape_clear(void* body, uint32_t n_labels, cudaStream_t s) {
+  return cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
+}
+
+cudaError_t shape_accumulate(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                             WsHeader* hdr, void* body, int z_lo, int z_hi, cudaStream_t s, uint32_t min_lt2) {
+  const ShapeAcc acc = acc_layout(body, n_labels);
+  if (z_hi <= z_lo) return cudaSuccess;
   if (min_lt2 > 1) {  // (every object voxel has LT2 >= 1: thresholds 0 and 1 filter nothing)
     if (d.ndim == 3)
-      launch_reduce<3, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, s);
+      launch_reduce<3, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, z_lo, z_hi, s);
     else
-      launch_reduce<2, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, s);
+      launch_reduce<2, true>(labels, lt2, n_labels, d, acc, hdr, min_lt2, z_lo, z_hi, s);
   } else if (d.ndim == 3) {
-    launch_reduce<3, false>(labels, lt2, n_labels, d, acc, hdr, 0u, s);
+    launch_reduce<3, false>(labels, lt2, n_labels, d, acc, hdr, 0u, z_lo, z_hi, s);
   } else {
-    launch_reduce<2, false>(labels, lt2, n_labels, d, acc, hdr, 0u, s);
+    launch_reduce<2, false>(labels, lt2, n_labels, d, acc, hdr, 0u, z_lo, z_hi, s);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t shape_finalize(int ndim, uint32_t n_labels, void* body, float* S, float* R,
+                           const lt_object_stats* stats, cudaStream_t s) {
+  const ShapeAcc acc = acc_layout(body, n_labels);
   lt_object_stats st = {nullptr, nullptr, nullptr, nullptr, nullptr};
   if (stats) st = *stats;
   const unsigned blocks = (n_labels + 255) / 256;
   {
     TraceScope t("shape_finalize", s);
-    if (d.ndim == 3)
+    if (ndim == 3)
       shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
     else
       shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
   }
   return cudaGetLastError();
+}
+
+cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels,
+                         const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
+                         const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2) {
+  cudaError_t e = shape_clear(body, n_labels, s);
+  if (e == cudaSuccess) e = shape_accumulate(labels, lt2, n_labels, d, hdr, body, 0, d.nz, s, min_lt2);
+  if (e == cudaSuccess) e = shape_finalize(d.ndim, n_labels, body, S, R, stats, s);
+  return e;
 }
 
 }  // namespace ltk
