@@ -526,6 +526,7 @@ struct Centre {
   int ddx, ddy, ddz, r2d;  // dominant neighbour offset and its r^2 (-1: none)
   int start, nseg;         // first item of this centre in the chunk; dy segments
   float inv_nseg;
+  int eoff[2], er2[2];     // 3D row mode: two more higher-ranked balls, offset code and r^2 (-1: none)
 };
 constexpr int kRowSeg = 8;  // rows per row-mode work item
 
@@ -611,6 +612,16 @@ __device__ __forceinline__ int make_centre(uint4 rec, const Dims& d, size_t sy, 
   }
   c.nseg = (2 * c.R + kRowSeg) / kRowSeg;
   c.inv_nseg = 1.0f / (float)c.nseg;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint32_t ec = (rec.z >> (5 * q)) & 31u;
+    c.eoff[q] = (int)ec;
+    c.er2[q] = -1;
+    if (NDIM == 3 && ec != kNoDominant) {
+      const int ez = (int)(ec / 9) - 1, ey = (int)(ec / 3 % 3) - 1, ex = (int)(ec % 3) - 1;
+      c.er2[q] = (int)dt2[(int64_t)idx + ez * (int64_t)sz + ey * (int64_t)sy + ex];
+    }
+  }
   return (NDIM == 3 ? 2 * c.R + 1 : 1) * c.nseg;
 }
 
@@ -764,15 +775,38 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, const Dims& d
       const int h = (int)c.r2 - dz * dz - dy * dy;
       if (h >= 0 && z >= 0 && z < d.nz && y >= 0 && y < d.ny) {
         w = (int)isqrt24((uint32_t)h);
-        int hi1 = w, lo2 = 1, hi2 = 0;
-        if (c.r2d >= 0) {
-          const int hd = c.r2d - (dz - c.ddz) * (dz - c.ddz) - (dy - c.ddy) * (dy - c.ddy);
-          if (hd >= 0) {
-            const int wd = (int)isqrt24((uint32_t)hd);
-            hi1 = min(w, c.ddx - wd - 1);
-            lo2 = max(-w, c.ddx + wd + 1);
-            hi2 = w;
+        // this row of the higher-ranked balls (dominant first, then the two
+        // extras) as one interval [elo, ehi] of dx: an extra's row joins
+        // only when it touches the interval so far (skipping one excludes
+        // less, which only paints more true-ball voxels)
+        int elo = 1, ehi = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          int rr, ox, oy, oz;
+          if (q == 0) {
+            rr = c.r2d, ox = c.ddx, oy = c.ddy, oz = c.ddz;
+          } else {
+            const int ec = c.eoff[q - 1];
+            rr = c.er2[q - 1], ox = ec % 3 - 1, oy = ec / 3 % 3 - 1, oz = ec / 9 - 1;
           }
+          if (rr < 0) continue;
+          const int hd = rr - (dz - oz) * (dz - oz) - (dy - oy) * (dy - oy);
+          if (hd < 0) continue;
+          const int wd = (int)isqrt24((uint32_t)hd);
+          const int lo = ox - wd, hi = ox + wd;
+          if (elo > ehi) {
+            elo = lo;
+            ehi = hi;
+          } else if (lo <= ehi + 1 && hi >= elo - 1) {
+            elo = min(elo, lo);
+            ehi = max(ehi, hi);
+          }
+        }
+        int hi1 = w, lo2 = 1, hi2 = 0;
+        if (elo <= ehi) {
+          hi1 = min(w, elo - 1);
+          lo2 = max(-w, ehi + 1);
+          hi2 = w;
         }
         a1 = max(-w, xmin);
         n1 = max(0, min(hi1, xmax) - a1 + 1);
