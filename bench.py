@@ -159,7 +159,8 @@ def cpu_oracle_rate(mask, labels, n_labels, target_s=15.0):
         if dt >= target_s / 3 or t >= nz:
             break
         t = min(nz, max(t * 2, int(t * target_s / max(dt, 1e-3) / 2)))
-    return m.size / dt / 1e6, f"z-slab {m.shape[0]}x{m.shape[1]}x{m.shape[2]} of the workload", dt
+    what = "x".join(str(v) for v in m.shape)
+    return m.size / dt / 1e6, f"{'rows' if m.ndim == 2 else 'z-slab'} {what} of the workload", dt
 
 
 def measure_batch(lt, args, dev):

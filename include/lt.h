@@ -117,8 +117,9 @@ lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64
  * its ball that one chosen higher-ranked neighbour's ball does not hold.
  * Neither step changes the maximum (proof in the kernel source).
  * Device-detected error: LT_ERR_LABEL_OUTSIDE_MASK.
- * Workspace: lt_local_thickness_workspace_size bytes (16 bytes per voxel for
- * the centre list). The first call on a device also copies lookup tables
+ * Workspace: lt_local_thickness_workspace_size bytes (18 bytes per voxel for
+ * the centre list: up to one 16-byte record per voxel, plus part records of
+ * big balls that several warps share). The first call on a device also copies lookup tables
  * (about 13 MiB, built once per process on the host) into device memory
  * owned by the library; make that first call before any stream capture. */
 size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
@@ -323,7 +324,7 @@ lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_lab
 
 /* Slab form of lt_measure for volumes held in host memory whose working set
  * does not fit the device (or a budget on it): the device works on
- * `slab_planes` z planes at a time (workspace ~28 bytes per voxel of a slab,
+ * `slab_planes` z planes at a time (workspace ~30 bytes per voxel of a slab,
  * lt_measure_slabs_workspace_size). Results equal lt_measure's bit for bit.
  * Phases: x/y EDT passes per slab (the y pass's output goes to dt2_host);
  * the z pass per band of rows over all z (2D copies, in place in dt2_host,

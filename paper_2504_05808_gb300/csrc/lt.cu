@@ -67,6 +67,14 @@ constexpr int kCresMaxVoxels = 2304 * 1024;  // both orderings (about 2.16 M vox
 constexpr uint32_t kNoDominant = 31u;
 constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a crescent table
 constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
+constexpr int kChunkR2D = 64;   // 2D: largest r^2 painted in shared chunks (bigger discs: a warp each)
+constexpr uint32_t kParts = 4;          // warps sharing one big row-mode centre, at most
+constexpr uint32_t kStepsPerPart = 12;  // row steps (32 rows each) per sharing warp, at least
+
+// Centre records: at most one per voxel, plus the extra part records of the
+// shared row-mode centres (at most n/8). The front list starts at 0, the
+// back list at the last slot.
+__host__ __device__ __forceinline__ size_t record_capacity(uint32_t n) { return (size_t)n + n / 8 + kParts; }
 constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
@@ -234,7 +242,9 @@ __device__ __forceinline__ uint32_t cres_combo(const uint32_t* base, int cls, ui
 //   each, 0xFF none).
 //   Painting needs no other lookup.
 //   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
-//   z = the two extra codes.
+//   z = the two extra codes; w = part | parts << 8 (row-mode centres go to
+//   the back list directly; a big one as up to kParts records, one per
+//   part, while the extra records stay within n/8).
 constexpr int kTX = 32, kTY = 8;
 constexpr int kOX = 4;                             // halo column of x0 (keeps TMA x 16-byte aligned)
 constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 40 x 10 words
@@ -476,8 +486,21 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           rec = make_uint4(v, r2 | (code << 25), extra, 0u);
         }
         // small crescents are shared out in chunks; a big one takes a warp
-        keepA = tab && (NDIM == 2 || best <= (uint32_t)kChunkCres);
+        keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= (uint32_t)kChunkCres);
         keepB = !keepA;
+        if (keepB && (NDIM == 2 || !tab)) {
+          // painted row by row, written at once (these centres are rare):
+          // a big ball as kParts records, one per warp sharing it (w = part
+          // | parts << 8), while the extra records fit their budget of n/8
+          keepB = false;
+          const int side = 2 * (int)isqrt24(r2) + 1;
+          const uint32_t steps = (uint32_t)((NDIM == 3 ? side * side : side) + 31) / 32;  // row steps
+          uint32_t parts = min(kParts, max(1u, steps / kStepsPerPart));
+          if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
+          const uint32_t base = atomicAdd(&hdr->n_big, parts);
+          for (uint32_t q = 0; q < parts; ++q)
+            surv[record_capacity(d.n) - 1 - (base + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 8));
+        }
       }
     }
     // at most kListBuf records between flushes: list A grows from the front
@@ -508,7 +531,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       }
       __syncthreads();
       for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = buf[i];
-      for (uint32_t i = tid; i < cntB; i += 256) surv[(size_t)d.n - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
+      for (uint32_t i = tid; i < cntB; i += 256) surv[record_capacity(d.n) - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
       __syncthreads();
       if (tid == 0) cntA = cntB = 0;
     }
@@ -753,24 +776,31 @@ __device__ __forceinline__ int owner_lane(int start, int k) {
   return j;
 }
 
-// One 3D row-mode centre, one warp: the lanes take 32 rows (dz, dy) of the
+// One row-mode centre, one warp: the lanes take 32 rows (dz, dy) of the
 // ball at a time and compute each row's crescent spans (the row of the ball
 // minus the dominant neighbour's row, clamped to the array); then the spans'
 // voxels are shared out in order, so consecutive lanes update consecutive x.
-__device__ __forceinline__ void paint_centre_rows(const Centre& c, const Dims& d, size_t sy, size_t sz,
+// Part p of `parts` takes the row steps p, p + parts, ...
+template <int NDIM>
+__device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int parts, const Dims& d, size_t sy,
+                                                  size_t sz,
                                                   bool touch, const uint32_t* __restrict__ dt2,
                                                   const uint32_t* __restrict__ labels,
                                                   uint32_t* __restrict__ lt2, uint32_t& nupd) {
   const int lane = threadIdx.x & 31;
-  const int side = 2 * c.R + 1, nrows = side * side;
+  const int side = 2 * c.R + 1, nrows = NDIM == 3 ? side * side : side;
   const int xmin = -c.cx, xmax = d.nx - 1 - c.cx;
-  for (int r0 = 0; r0 < nrows; r0 += 32) {
+  for (int r0 = part * 32; r0 < nrows; r0 += 32 * parts) {
     const int r = r0 + lane;
     int a1 = 0, n1 = 0, a2 = 0, n2 = 0, w = -1;  // spans [a1, a1 + n1), [a2, a2 + n2) of dx
     uint32_t rowbase = 0;                        // linear index of (cx, y, z)
     if (r < nrows) {
-      const int q = r / side;
-      const int dz = q - c.R, dy = r - q * side - c.R;
+      int dz = 0, dy = r - c.R;  // 2D: one row per dy
+      if (NDIM == 3) {
+        const int q = r / side;
+        dz = q - c.R;
+        dy = r - q * side - c.R;
+      }
       const int z = c.cz + dz, y = c.cy + dy;
       const int h = (int)c.r2 - dz * dz - dy * dy;
       if (h >= 0 && z >= 0 && z < d.nz && y >= 0 && y < d.ny) {
@@ -837,10 +867,16 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, const Dims& d
 }
 
 // Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
-// crescent voxels, two per lane in flight. A warp takes kChunkGrab chunks
-// per counter update (one hot counter serialises its atomics).
-constexpr int kChunkGrab = 4;
-constexpr int kBigGrab = 2;  // phase 1 centres per counter update
+// crescent voxels, two per lane in flight. A warp takes several chunks per
+// counter update when there is plenty of work (one hot counter serialises
+// its atomics), one at a time otherwise (so that small inputs still spread
+// over all warps).
+__device__ __forceinline__ uint32_t grab_size(uint32_t items, uint32_t most) {
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  return items >= 2u * most * warps ? most : 1u;
+}
+constexpr uint32_t kChunkGrab = 4;  // chunks per counter update, at most
+constexpr uint32_t kBigGrab = 2;    // phase 1 centres per counter update, at most
 __device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
                                                    size_t sy, size_t sz, bool touch,
                                                    const uint32_t* __restrict__ dt2,
@@ -850,12 +886,13 @@ __device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ sur
   __shared__ TabCentre cs[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t nchunks = (n + 31) / 32;
+  const uint32_t grab = grab_size(nchunks, kChunkGrab);
   uint32_t ch = 0, grab_end = 0;
   for (;;) {
-    if (ch == grab_end) {  // the next kChunkGrab chunks from the shared counter
-      if (lane == 0) ch = atomicAdd(&hdr->ctr_small, (uint32_t)kChunkGrab);
+    if (ch == grab_end) {  // the next chunks from the shared counter
+      if (lane == 0) ch = atomicAdd(&hdr->ctr_small, grab);
       ch = __shfl_sync(kFull, ch, 0);
-      grab_end = ch + kChunkGrab;
+      grab_end = ch + grab;
     }
     if (ch >= nchunks) break;
     const uint32_t i = ch++ * 32 + lane;
@@ -931,10 +968,10 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
 }
 
 // Two phases, each fed by a global work counter.
-// 1. (3D) Centres from the back of the list, one per warp: the lanes share
-//    its crescent voxels (big table crescents) or its (2R+1) * ceil((2R+1)/8)
-//    row segments (row mode). These are the biggest pieces of work, so they
-//    go first.
+// 1. Centres from the back of the list, one per warp: the lanes share its
+//    crescent voxels (big 3D table crescents) or take its rows 32 at a time
+//    (row mode: 3D centres without a table, 2D discs with r^2 > 64). These
+//    are the biggest pieces of work, so they go first.
 // 2. Chunks of 32 centres from the front of the list: the 32 lanes share the
 //    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
 //    and small crescents balance.
@@ -950,17 +987,18 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   const bool touch = *(volatile uint32_t*)&hdr->touch != 0;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   uint32_t nupd = 0, ntab = 0;  // updates this thread issued: row by row, from tables
-  if (NDIM == 3) {
+  {
+    const uint32_t grab = grab_size(nbig, kBigGrab);
     uint32_t b = 0, grab_end = 0;
     for (;;) {
-      if (b == grab_end) {  // the next kBigGrab centres from the shared counter
-        if (lane == 0) b = atomicAdd(&hdr->ctr_big, (uint32_t)kBigGrab);
+      if (b == grab_end) {  // the next records from the shared counter
+        if (lane == 0) b = atomicAdd(&hdr->ctr_big, grab);
         b = __shfl_sync(kFull, b, 0);
-        grab_end = b + kBigGrab;
+        grab_end = b + grab;
       }
       if (b >= nbig) break;
-      const uint4 rec = surv[(size_t)d.n - 1 - b++];
-      if (rec.z & kTableRecord) {
+      const uint4 rec = surv[record_capacity(d.n) - 1 - b++];
+      if (NDIM == 3 && (rec.z & kTableRecord)) {
         TabCentre c;
         const int items = make_tab_centre(rec, sy, sz, touch, labels, c);
         for (int k = lane; k < items; k += 32) {
@@ -974,14 +1012,16 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
         }
       } else {
         Centre c;
-        make_centre<3>(rec, d, sy, sz, touch, dt2, labels, c);
-        paint_centre_rows(c, d, sy, sz, touch, dt2, labels, lt2, nupd);
+        make_centre<NDIM>(rec, d, sy, sz, touch, dt2, labels, c);
+        paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFu), max(1, (int)(rec.w >> 8)), d, sy, sz, touch, dt2,
+                                labels, lt2, nupd);
       }
     }
-    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
-  } else {
-    paint_row_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, nupd);
   }
+  if (NDIM == 3)
+    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
+  else
+    paint_row_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, nupd);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     nupd += __shfl_xor_sync(kFull, nupd, o);
@@ -1025,7 +1065,7 @@ bool make_tensor_map_u32_3d(CUtensorMap* map, const void* base, int nx, int ny, 
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t lt_workspace_bytes(const Dims& d) { return align_up((size_t)d.n * sizeof(uint4)); }
+size_t lt_workspace_bytes(const Dims& d) { return align_up(record_capacity(d.n) * sizeof(uint4)); }
 
 cudaError_t lt_prepare_device() { return ensure_tables(); }
 

@@ -28,7 +28,8 @@ struct WsHeader {
   unsigned long long n_updates;        // LT2 updates (atomic max) the paint kernel issued
   unsigned long long n_table_updates;  // of which from crescent tables
   uint32_t max_dt2;                    // slab pipeline: largest DT2 of the volume
-  uint32_t reserved[53];
+  uint32_t n_extra;                    // extra part records of shared row-mode centres
+  uint32_t reserved[52];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 

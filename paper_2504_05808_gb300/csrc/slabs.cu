@@ -51,10 +51,11 @@ size_t acc_region(uint32_t n_labels) {
 }  // namespace
 
 // Region for a slab of P planes: phase 3 needs DT2, labels, LT2 and the
-// centre records (28 bytes per voxel); phases 1 and 2 fit in it.
+// local-thickness scratch (30 bytes per voxel); phases 1 and 2 fit in it.
 size_t slabs_ws_bytes(uint32_t n_labels, int nx, int ny, int P) {
-  const size_t plane = (size_t)nx * ny;
-  return sizeof(WsHeader) + acc_region(n_labels) + 28 * (size_t)P * plane + 4 * kAlign;
+  const size_t n = (size_t)P * nx * ny;
+  return sizeof(WsHeader) + acc_region(n_labels) + 3 * align_up(n * 4) + lt_workspace_bytes(sub_dims(nx, ny, P)) +
+         4 * kAlign;
 }
 
 lt_status slabs_run(const uint8_t* mask_h, const uint32_t* labels_h, uint32_t n_labels, int nx, int ny, int nz,
@@ -127,6 +128,7 @@ lt_status slabs_run(const uint8_t* mask_h, const uint32_t* labels_h, uint32_t n_
     if (!ok(cudaMemcpyAsync(dt2, dt2_h + (size_t)e0 * plane, (size_t)d.n * 4, cudaMemcpyHostToDevice, s)) ||
         !ok(cudaMemcpyAsync(lab, labels_h + (size_t)e0 * plane, (size_t)d.n * 4, cudaMemcpyHostToDevice, s)) ||
         !ok(cudaMemsetAsync(&hdr->n_surv, 0, offsetof(WsHeader, n_updates) - offsetof(WsHeader, n_surv), s)) ||
+        !ok(cudaMemsetAsync(&hdr->n_extra, 0, sizeof(uint32_t), s)) ||
         !ok(lt_launch(dt2, lab, lt2, d, hdr, q, s)) ||
         !ok(shape_accumulate(lab, lt2, n_labels, d, hdr, acc, z0 - e0, z0 - e0 + c, s)))
       return LT_ERR_CUDA;
