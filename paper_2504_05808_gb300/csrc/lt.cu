@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   __shared__ uint4 buf[kListBuf];
   __shared__ uint16_t work[256];
   __shared__ __align__(8) uint64_t bar[kSlots];
-  __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s;
+  __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s, nkept_s;
+  __shared__ uint4 keptq[256];  // pass 2a -> 2b: tile position, per-class best keys
   __shared__ uint32_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 1];  // copy of g_cres_base
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
     cntA = cntB = 0;
     // after a timeout anywhere in this launch, the remaining CTAs stop at once
     flags = TMA && (*(volatile uint32_t*)&hdr->error & ERR_TIMEOUT) ? 4u : 0u;
-    nwork_s = 0;
+    nwork_s = nkept_s = 0;
     if (TMA) {
       for (int s = 0; s < kSlots; ++s) mbar_init(&bar[s], 1);
       fence_barrier_init();
@@ -386,9 +387,11 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
     }
     __syncthreads();
     const uint32_t nwork = nwork_s;
-    // pass 2, compacted labelled foreground voxels: containment test
-    bool keepA = false, keepB = false;
-    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+    // pass 2a, compacted labelled foreground voxels: containment test; the
+    // kept ones are compacted again (with their per-class best keys) so that
+    // pass 2b, which builds their records, runs on full warps
+    bool kept = false;
+    uint4 kinfo = make_uint4(0u, 0u, 0u, 0u);
     if ((uint32_t)tid < nwork) {
       const int t = work[tid];
       const int tx = t & 31, ty = t >> 5;
@@ -423,17 +426,45 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
         }
       }
       bool pruned = false;
+#pragma unroll
+      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k) pruned = pruned || (int)(kmax[k] >> 6) >= m[k];
+      kept = !pruned;
+      kinfo = make_uint4((uint32_t)t, kmax[0], kmax[1], kmax[2]);
+    }
+    {
+      const unsigned bk = __ballot_sync(kFull, kept);
+      uint32_t off = 0;
+      if (lane == 0 && bk) off = atomicAdd(&nkept_s, (uint32_t)__popc(bk));
+      off = __shfl_sync(kFull, off, 0);
+      if (kept) keptq[off + __popc(bk & below)] = kinfo;
+    }
+    __syncthreads();
+    const uint32_t nkept = nkept_s;
+    // pass 2b, kept centres: dominant, extras and the record
+    bool keepA = false, keepB = false;
+    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+    if ((uint32_t)tid < nkept) {
+      const uint4 kq = keptq[tid];
+      const int t = (int)kq.x;
+      const int tx = t & 31, ty = t >> 5;
+      const int c = (ty + 1) * kBX + (tx + kOX);
+      const uint32_t r2 = D0[c];
+      const uint32_t kmax[3] = {kq.y, kq.z, kq.w};
+      int m[3] = {kNoTable, kNoTable, kNoTable};
+      if (r2 <= kMCap) {
+        m[0] = (int)mt[r2];
+        m[1] = (int)mt[(kMCap + 1) + r2];
+        if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
+      }
       int brn[3] = {-1, -1, -1};
       uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
 #pragma unroll
-      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k) {
-        pruned = pruned || (int)(kmax[k] >> 6) >= m[k];
+      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
         if ((kmax[k] >> 5) > 2 * r2) {
           brn[k] = (int)(kmax[k] >> 6);
           bcode[k] = kmax[k] & 31u;
         }
-      }
-      if (!pruned) {
+      {
         uint32_t code = kNoDominant, vstart = 0, best = UINT_MAX;
         int kd = -1;
         if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
@@ -523,7 +554,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       fence_proxy_async();
       issue(z + 3);
     }
-    if (tid == 0) nwork_s = 0;
+    if (tid == 0) nwork_s = nkept_s = 0;
     if (cntA + cntB > kListBuf - 256 || z + 1 == z1) {  // uniform: read after the barrier
       if (tid == 0) {
         baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
