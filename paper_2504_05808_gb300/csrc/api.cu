@@ -2,6 +2,7 @@
 // layout, device selection and the launch sequence. All compute is in the
 // kernels of edt.cu, lt.cu and shape.cu.
 #include <cstring>
+#include <mutex>
 
 #include "lt_internal.cuh"
 
@@ -274,6 +275,20 @@ static size_t host_layout(const Dims& d, uint32_t n_labels, size_t off[6]) {
   return p;
 }
 
+constexpr int kHostSlabs = 8;  // z-slabs of the mask copy in lt_measure_host
+
+// One non-blocking copy stream per device, created on first use and kept.
+static cudaStream_t copy_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
 size_t lt_measure_host_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz) {
   Dims d;
   if (make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
@@ -300,11 +315,48 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
   float* S = reinterpret_cast<float*>(base + off[4]);
   float* R = reinterpret_cast<float*>(base + off[5]);
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = cudaMemcpyAsync(mask, mask_host, (size_t)d.n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(labels, labels_host, (size_t)d.n * 4, cudaMemcpyHostToDevice, s);
+  // The copies run on a second stream so that they overlap the work: the
+  // mask arrives in z-slabs, each slab's x and y EDT passes start as soon as
+  // it is there, and the labels (needed from the ridge pass on) arrive
+  // while the EDT runs.
+  cudaStream_t c = copy_stream();
+  if (!c) return LT_ERR_CUDA;
+  const int K = d.ndim == 3 ? std::min(d.nz, kHostSlabs) : 1;
+  cudaEvent_t ev[kHostSlabs + 1];
+  for (int k = 0; k <= K; ++k)
+    if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
+      return LT_ERR_CUDA;
+    }
+  const size_t plane = (size_t)d.nx * d.ny;
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
+  cudaError_t e = cudaEventRecord(ev[K], s);  // the copies start after earlier work on `stream`
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c, ev[K], 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const int z0 = (int)((int64_t)d.nz * k / K), z1 = (int)((int64_t)d.nz * (k + 1) / K);
+    e = cudaMemcpyAsync(mask + z0 * plane, mask_host + z0 * plane, (size_t)(z1 - z0) * plane,
+                        cudaMemcpyHostToDevice, c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[k], c);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(labels, labels_host, (size_t)d.n * 4, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[K], c);
+  const Tuning tu;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const int z0 = (int)((int64_t)d.nz * k / K), z1 = (int)((int64_t)d.nz * (k + 1) / K);
+    Dims dk = d;
+    dk.nz = z1 - z0;
+    dk.n = (uint32_t)((size_t)dk.nz * plane);
+    e = cudaStreamWaitEvent(s, ev[k], 0);
+    if (e == cudaSuccess) e = edt_launch(mask + z0 * plane, dt2 + z0 * plane, dk, body, s, tu, 1);
+  }
+  if (e == cudaSuccess) e = edt_launch(nullptr, dt2, d, body, s, tu, 2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[K], 0);
+  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s, tu);
+  if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
+  for (int k = 0; k <= K; ++k) cudaEventDestroy(ev[k]);  // (released once the stream is past them)
   if (e != cudaSuccess) return LT_ERR_CUDA;
-  st = run_measure(mask, labels, n_labels, d, ws, dt2, lt2, S, R, s);
-  if (st != LT_OK) return st;
   e = cudaMemcpyAsync(sphericity_host, S, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(roundness_host, R, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return LT_ERR_CUDA;
