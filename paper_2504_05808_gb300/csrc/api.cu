@@ -315,47 +315,64 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
   float* S = reinterpret_cast<float*>(base + off[4]);
   float* R = reinterpret_cast<float*>(base + off[5]);
   cudaStream_t s = as_stream(stream);
-  // The copies run on a second stream so that they overlap the work: the
-  // mask arrives in z-slabs, each slab's x and y EDT passes start as soon as
-  // it is there, and the labels (needed from the ridge pass on) arrive
-  // while the EDT runs.
+  // The copies run on a second stream and overlap the work: the mask
+  // arrives in z-slabs, each slab's x and y EDT passes start as soon as it
+  // is there; the labels arrive in z-slabs during the EDT, and the ridge
+  // pass runs slab by slab as they land (a slab also needs the next slab's
+  // first plane). Painting needs every centre (and the `touch` flag of the
+  // whole volume), so it starts after the last ridge slab.
   cudaStream_t c = copy_stream();
   if (!c) return LT_ERR_CUDA;
+  const Tuning tu;
   const int K = d.ndim == 3 ? std::min(d.nz, kHostSlabs) : 1;
-  cudaEvent_t ev[kHostSlabs + 1];
-  for (int k = 0; k <= K; ++k)
+  const int rz = ridge_chunk(tu), nch = (d.nz + rz - 1) / rz;
+  const int KL = d.ndim == 3 ? std::min(nch, kHostSlabs) : 1;  // label slabs: whole ridge chunks
+  cudaEvent_t ev[2 * kHostSlabs + 1];
+  const int nev = K + KL + 1;
+  for (int k = 0; k < nev; ++k)
     if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
       for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
       return LT_ERR_CUDA;
     }
+  cudaEvent_t* ev_mask = ev;
+  cudaEvent_t* ev_lab = ev + K;
+  cudaEvent_t ev_start = ev[K + KL];
   const size_t plane = (size_t)d.nx * d.ny;
+  auto lab_z = [&](int k) { return d.ndim == 3 ? std::min(d.nz, (int)((int64_t)nch * k / KL) * rz) : 0; };
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
   void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
-  cudaError_t e = cudaEventRecord(ev[K], s);  // the copies start after earlier work on `stream`
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c, ev[K], 0);
+  cudaError_t e = cudaEventRecord(ev_start, s);  // the copies start after earlier work on `stream`
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c, ev_start, 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     const int z0 = (int)((int64_t)d.nz * k / K), z1 = (int)((int64_t)d.nz * (k + 1) / K);
     e = cudaMemcpyAsync(mask + z0 * plane, mask_host + z0 * plane, (size_t)(z1 - z0) * plane,
                         cudaMemcpyHostToDevice, c);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[k], c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_mask[k], c);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(labels, labels_host, (size_t)d.n * 4, cudaMemcpyHostToDevice, c);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[K], c);
-  const Tuning tu;
+  for (int k = 0; k < KL && e == cudaSuccess; ++k) {
+    const int z0 = lab_z(k), z1 = d.ndim == 3 ? lab_z(k + 1) : 1;
+    const size_t pl = d.ndim == 3 ? plane : (size_t)d.n;
+    e = cudaMemcpyAsync(labels + z0 * pl, labels_host + z0 * pl, (size_t)(z1 - z0) * pl * 4,
+                        cudaMemcpyHostToDevice, c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_lab[k], c);
+  }
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     const int z0 = (int)((int64_t)d.nz * k / K), z1 = (int)((int64_t)d.nz * (k + 1) / K);
     Dims dk = d;
     dk.nz = z1 - z0;
     dk.n = (uint32_t)((size_t)dk.nz * plane);
-    e = cudaStreamWaitEvent(s, ev[k], 0);
+    e = cudaStreamWaitEvent(s, ev_mask[k], 0);
     if (e == cudaSuccess) e = edt_launch(mask + z0 * plane, dt2 + z0 * plane, dk, body, s, tu, 1);
   }
   if (e == cudaSuccess) e = edt_launch(nullptr, dt2, d, body, s, tu, 2);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[K], 0);
-  if (e == cudaSuccess) e = lt_launch(dt2, labels, lt2, d, hdr, body, s, tu);
+  for (int k = 0; k < KL && e == cudaSuccess; ++k) {
+    e = cudaStreamWaitEvent(s, ev_lab[std::min(k + 1, KL - 1)], 0);  // (copies land in order)
+    if (e == cudaSuccess) e = lt_ridge_launch(dt2, labels, lt2, d, hdr, body, s, tu, lab_z(k), d.ndim == 3 ? lab_z(k + 1) : 1);
+  }
+  if (e == cudaSuccess) e = lt_paint_launch(dt2, labels, lt2, d, hdr, body, s, tu);
   if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
-  for (int k = 0; k <= K; ++k) cudaEventDestroy(ev[k]);  // (released once the stream is past them)
+  for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);  // (released once the streams are past them)
   if (e != cudaSuccess) return LT_ERR_CUDA;
   e = cudaMemcpyAsync(sphericity_host, S, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(roundness_host, R, (size_t)n_labels * 4, cudaMemcpyDeviceToHost, s);

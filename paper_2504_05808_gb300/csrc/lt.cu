@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
                                                        uint4* __restrict__ surv,
-                                                       WsHeader* __restrict__ hdr, RidgeWait wt) {
+                                                       WsHeader* __restrict__ hdr, RidgeWait wt, int z_base) {
   __shared__ __align__(128) uint32_t sD[kSlots][kSlotPitch];
   __shared__ __align__(128) uint32_t sL[kSlots][kSlotPitch];
   __shared__ uint4 buf[kListBuf];
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   __shared__ uint32_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 1];  // copy of g_cres_base
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int z0 = NDIM == 3 ? blockIdx.z * RZ : 0;
+  const int z0 = NDIM == 3 ? blockIdx.z * RZ + z_base : 0;
   const int z1 = NDIM == 3 ? min(d.nz, z0 + RZ) : 1;
   const size_t plane = (size_t)d.nx * d.ny;
   const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
@@ -1067,11 +1067,11 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
 template <int NDIM, int RZ>
 void launch_ridge(bool tma, dim3 grid, cudaStream_t s, const CUtensorMap& md, const CUtensorMap& ml,
                   const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d, uint4* surv,
-                  WsHeader* hdr, RidgeWait wt = RidgeWait()) {
+                  WsHeader* hdr, RidgeWait wt = RidgeWait(), int z_base = 0) {
   if (tma)
-    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt);
+    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base);
   else
-    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt);
+    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base);
 }
 
 }  // namespace
@@ -1134,32 +1134,47 @@ cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
-                      WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {
+int ridge_chunk(const Tuning& tu) { return tu.ridge_z == 8 || tu.ridge_z == 32 ? tu.ridge_z : 16; }
+
+cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
   uint4* surv = reinterpret_cast<uint4*>(body);
-  const int rz = tu.ridge_z == 8 || tu.ridge_z == 32 ? tu.ridge_z : 16;
-  dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY, d.ndim == 3 ? (d.nz + rz - 1) / rz : 1);
+  const int rz = ridge_chunk(tu);
+  if (d.ndim == 2) {
+    z_lo = 0;
+    z_hi = 1;
+  } else if (z_hi < 0 || z_hi > d.nz) {
+    z_hi = d.nz;
+  }
+  const int c_lo = z_lo / rz, c_hi = (z_hi + rz - 1) / rz;  // z_lo is a multiple of rz
+  if (c_hi <= c_lo) return cudaSuccess;
+  dim3 grid((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY, d.ndim == 3 ? c_hi - c_lo : 1);
   // TMA needs a row pitch that is a multiple of 16 bytes
   CUtensorMap md, ml;
   std::memset(&md, 0, sizeof(md));
   std::memset(&ml, 0, sizeof(ml));
   const bool tma = d.nx % 4 == 0 && make_tensor_map_u32_3d(&md, dt2, d.nx, d.ny, d.nz, kBX, kBY) &&
                    make_tensor_map_u32_3d(&ml, labels, d.nx, d.ny, d.nz, kBX, kBY);
+  const int zb = c_lo * rz;
   {
     TraceScope t("lt_ridge", s);
     if (d.ndim == 2)
       launch_ridge<2, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
     else if (rz == 8)
-      launch_ridge<3, 8>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 8>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
     else if (rz == 32)
-      launch_ridge<3, 32>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 32>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
     else
-      launch_ridge<3, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<3, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {
+  const uint4* surv = reinterpret_cast<const uint4*>(body);
   const int bps = tu.paint_blocks_per_sm > 0 ? tu.paint_blocks_per_sm : 8;
   const unsigned pblocks = (unsigned)(sm_count() * bps);
   {
@@ -1170,6 +1185,13 @@ cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2
       lt_paint_kernel<2><<<pblocks, 256, 0, s>>>(surv, dt2, labels, lt2, d, hdr);
   }
   return cudaGetLastError();
+}
+
+cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                      WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {
+  cudaError_t e = lt_ridge_launch(dt2, labels, lt2, d, hdr, body, s, tu, 0, d.nz);
+  if (e == cudaSuccess) e = lt_paint_launch(dt2, labels, lt2, d, hdr, body, s, tu);
+  return e;
 }
 
 }  // namespace ltk

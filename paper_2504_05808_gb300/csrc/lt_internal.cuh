@@ -76,6 +76,14 @@ cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* 
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                       WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu = Tuning());
+// the two stages of lt_launch: the ridge pass over planes [z_lo, z_hi)
+// (z_lo a multiple of ridge_chunk(tu); its planes and the one on either side
+// must hold final DT2 and labels), then the painting of every kept centre
+int ridge_chunk(const Tuning& tu);
+cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi);
+cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu);
 // timeout self-test of the ridge kernel's bounded waits (see lt.h)
 size_t ridge_selftest_bytes();
 cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);

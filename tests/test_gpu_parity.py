@@ -214,17 +214,27 @@ def test_device_detected_errors(lt):
 
 
 def test_host_buffer_entry_matches_device_path(lt):
+    """The host-buffer entry copies in z-slabs and runs the ridge pass slab by
+    slab as the labels land; it must give the device path's bits, also for
+    slab counts that do not divide the volume and in 2D."""
     import torch
-    m, l, n = synth.workload("ellipsoids_3d_128", 1)
-    _, _, S_dev, R_dev, _ = gpu_pipeline(lt, m, l, n)
-    mh = torch.from_numpy(m).pin_memory()
-    lh = torch.from_numpy(l.view(np.int32)).pin_memory()
-    Sh = torch.empty(n, dtype=torch.float32).pin_memory()
-    Rh = torch.empty(n, dtype=torch.float32).pin_memory()
-    ws = lt.workspace(lt.lt_measure_host_workspace_size(n, m.shape), "cuda")
-    lt.lt_measure_host(mh, lh, n, Sh, Rh, ws)
-    assert np.array_equal(Sh.numpy(), S_dev, equal_nan=True)
-    assert np.array_equal(Rh.numpy(), R_dev, equal_nan=True)
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(8)
+    f = ndi.gaussian_filter(rng.random((70, 45, 36)), 2.0)
+    rag = (f > np.quantile(f, 0.5)).astype(np.uint8)
+    rag_l = ndi.label(rag)[0].astype(np.uint32)
+    cases = [synth.workload("ellipsoids_3d_128", 1), synth.workload("ellipses_2d_256", 2),
+             (rag, rag_l, int(rag_l.max()) + 1)]
+    for m, l, n in cases:
+        _, _, S_dev, R_dev, _ = gpu_pipeline(lt, m, l, n)
+        mh = torch.from_numpy(m).pin_memory()
+        lh = torch.from_numpy(l.view(np.int32)).pin_memory()
+        Sh = torch.empty(n, dtype=torch.float32).pin_memory()
+        Rh = torch.empty(n, dtype=torch.float32).pin_memory()
+        ws = lt.workspace(lt.lt_measure_host_workspace_size(n, m.shape), "cuda")
+        lt.lt_measure_host(mh, lh, n, Sh, Rh, ws)
+        assert np.array_equal(Sh.numpy(), S_dev, equal_nan=True)
+        assert np.array_equal(Rh.numpy(), R_dev, equal_nan=True)
 
 
 def test_repeated_calls_reuse_workspace(lt):
