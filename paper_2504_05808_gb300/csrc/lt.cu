@@ -679,57 +679,90 @@ __device__ __forceinline__ int make_centre(uint4 rec, const Dims& d, size_t sy, 
   return (NDIM == 3 ? 2 * c.R + 1 : 1) * c.nseg;
 }
 
-// Table mode: a 3D centre with r^2 <= kCresT and a dominant neighbour,
-// decoded from its record alone (40 bytes, shared memory).
-struct TabCentre {
-  uint32_t idx, vstart, r2, label;
-  int S[3];       // signed linear strides of the canonical axes x, y, z
-  uint32_t ex;    // extra balls: r^2 (8 bits each, 0xFF none) | canonical offsets << 16 (6 bits each)
-  uint32_t axes;  // world axis (2 bits each) and sign bit (<< 6..8) of canonical x, y, z; inside << 9
-  int start;      // first crescent voxel of this centre in the chunk
+// Per-CTA lookup tables of the paint kernel (shared memory, built at launch):
+// integer square roots of small values, and for every dominant offset code
+// the canonical axis order and signs of its crescent, and the canonical
+// offset of every other neighbour under that order.
+constexpr int kSqrtLut = 4096;
+struct PaintLut {
+  uint8_t sq[kSqrtLut];  // floor(sqrt(v)), v < kSqrtLut
+  uint16_t perm[27];     // world axis of canonical x, y, z (2 bits each) | their sign bits << 6
+  uint8_t eo[27 * 27];   // [dominant code][neighbour code]: canonical offset, (o + 1) in 2 bits per axis
 };
 
 // Canonical x, y, z of a crescent: the nonzero axes of the dominant offset
 // first (in x, y, z order), then the zero axes; signs make the offset
-// (1,0,0), (1,1,0) or (1,1,1). Returns the crescent size.
+// (1,0,0), (1,1,0) or (1,1,1).
+__device__ void init_paint_lut(PaintLut& L) {
+  for (int i = threadIdx.x; i < kSqrtLut; i += blockDim.x) L.sq[i] = (uint8_t)isqrt24((uint32_t)i);
+  for (int i = threadIdx.x; i < 27 * 28; i += blockDim.x) {
+    const int code = i / 28, e = i % 28;  // e == 27: the permutation itself
+    const int ddz = code / 9 - 1, ddy = code / 3 % 3 - 1, ddx = code % 3 - 1;
+    const int cls = (ddx != 0) + (ddy != 0) + (ddz != 0);
+    int a0 = 0, a1 = 1, a2 = 2;
+    if (cls == 2) {
+      if (ddx == 0) { a0 = 1; a1 = 2; a2 = 0; }
+      else if (ddy == 0) { a0 = 0; a1 = 2; a2 = 1; }
+    } else if (cls == 1) {
+      if (ddy != 0) { a0 = 1; a1 = 0; a2 = 2; }
+      else if (ddz != 0) { a0 = 2; a1 = 0; a2 = 1; }
+    }
+    auto comp = [](int a, int vx, int vy, int vz) { return a == 0 ? vx : (a == 1 ? vy : vz); };
+    const int g0 = comp(a0, ddx, ddy, ddz) < 0, g1 = comp(a1, ddx, ddy, ddz) < 0, g2 = comp(a2, ddx, ddy, ddz) < 0;
+    if (e == 27) {
+      L.perm[code] = (uint16_t)(a0 | (a1 << 2) | (a2 << 4) | (g0 << 6) | (g1 << 7) | (g2 << 8));
+    } else {
+      const int ez = e / 9 - 1, ey = e / 3 % 3 - 1, ex = e % 3 - 1;
+      const int q0 = g0 ? -comp(a0, ex, ey, ez) : comp(a0, ex, ey, ez);
+      const int q1 = g1 ? -comp(a1, ex, ey, ez) : comp(a1, ex, ey, ez);
+      const int q2 = g2 ? -comp(a2, ex, ey, ez) : comp(a2, ex, ey, ez);
+      L.eo[code * 27 + e] = (uint8_t)((q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4));
+    }
+  }
+}
+
+__device__ __forceinline__ int isqrt_lut(const PaintLut& L, int v) {
+  return v < kSqrtLut ? (int)L.sq[v] : (int)isqrt24((uint32_t)v);
+}
+
+// Table mode: a 3D centre with r^2 <= kCresT and a dominant neighbour,
+// decoded from its record alone. In the shared chunks of phase 2 it is kept
+// as two 16-byte words (idx, vstart, start, r2ax) and (S, ex), plus the label.
+struct TabCentre {
+  uint32_t idx, vstart, start;
+  uint32_t r2ax;  // r^2 | world axis (2 bits each) and sign bit (<< 6..8) of canonical x, y, z << 8 | inside << 17
+  int S[3];       // signed linear strides of the canonical axes x, y, z
+  uint32_t ex;    // extra balls: r^2 (8 bits each, 0xFF none) | canonical offsets << 16 (6 bits each)
+  uint32_t label;
+};
+
+// Returns the crescent size.
 __device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, bool touch,
-                                               const uint32_t* __restrict__ labels, TabCentre& c) {
+                                               const uint32_t* __restrict__ labels, const PaintLut& L,
+                                               TabCentre& c) {
   c.idx = rec.x;
   c.vstart = rec.y & 0x3FFFFFu;
-  c.r2 = rec.z & 0xFFu;
+  c.start = 0;
   const uint32_t code = (rec.z >> 8) & 31u;
-  const int ddz = (int)(code / 9) - 1, ddy = (int)(code / 3 % 3) - 1, ddx = (int)(code % 3) - 1;
-  const int cls = (ddx != 0) + (ddy != 0) + (ddz != 0);
-  int a0 = 0, a1 = 1, a2 = 2;
-  if (cls == 2) {
-    if (ddx == 0) { a0 = 1; a1 = 2; a2 = 0; }
-    else if (ddy == 0) { a0 = 0; a1 = 2; a2 = 1; }
-  } else if (cls == 1) {
-    if (ddy != 0) { a0 = 1; a1 = 0; a2 = 2; }
-    else if (ddz != 0) { a0 = 2; a1 = 0; a2 = 1; }
-  }
-  auto comp = [](int a, int vx, int vy, int vz) { return a == 0 ? vx : (a == 1 ? vy : vz); };
+  const uint32_t pm = L.perm[code];
+  c.r2ax = (rec.z & 0xFFu) | (pm << 8) | (((rec.z >> 23) & 1u) << 17);
   const int sy_ = (int)sy, sz_ = (int)sz;
-  const int g0 = comp(a0, ddx, ddy, ddz) < 0, g1 = comp(a1, ddx, ddy, ddz) < 0, g2 = comp(a2, ddx, ddy, ddz) < 0;
-  c.axes = (uint32_t)(a0 | (a1 << 2) | (a2 << 4) | (g0 << 6) | (g1 << 7) | (g2 << 8)) | (((rec.z >> 23) & 1u) << 9);
-  const int t0 = comp(a0, 1, sy_, sz_), t1 = comp(a1, 1, sy_, sz_), t2 = comp(a2, 1, sy_, sz_);
-  c.S[0] = g0 ? -t0 : t0;
-  c.S[1] = g1 ? -t1 : t1;
-  c.S[2] = g2 ? -t2 : t2;
+  auto stride = [&](uint32_t a, uint32_t g) {
+    const int t = a == 0 ? 1 : (a == 1 ? sy_ : sz_);
+    return g ? -t : t;
+  };
+  c.S[0] = stride(pm & 3u, (pm >> 6) & 1u);
+  c.S[1] = stride((pm >> 2) & 3u, (pm >> 7) & 1u);
+  c.S[2] = stride((pm >> 4) & 3u, (pm >> 8) & 1u);
   uint32_t ex = 0;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const uint32_t ec = (rec.z >> (13 + 5 * q)) & 31u;
     uint32_t er = (rec.w >> (8 * q)) & 0xFFu, eo = 0;
-    if (ec == kNoDominant) {
+    if (ec == kNoDominant)
       er = 0xFFu;
-    } else {
-      const int ez = (int)(ec / 9) - 1, ey = (int)(ec / 3 % 3) - 1, exx = (int)(ec % 3) - 1;
-      const int q0 = g0 ? -comp(a0, exx, ey, ez) : comp(a0, exx, ey, ez);
-      const int q1 = g1 ? -comp(a1, exx, ey, ez) : comp(a1, exx, ey, ez);
-      const int q2 = g2 ? -comp(a2, exx, ey, ez) : comp(a2, exx, ey, ez);
-      eo = (uint32_t)((q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4));
-    }
+    else
+      eo = L.eo[code * 27 + ec];
     ex |= (er << (8 * q)) | (eo << (16 + 6 * q));
   }
   c.ex = ex;
@@ -751,7 +784,7 @@ __device__ __forceinline__ bool tab_voxel_index(const TabCentre& c, uint32_t p, 
     const int e0 = (int)(eo & 3u) - 1, e1 = (int)((eo >> 2) & 3u) - 1, e2 = (int)((eo >> 4) & 3u) - 1;
     if (er != 0xFF && (o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= er) return false;
   }
-  const uint32_t axes = c.axes;
+  const uint32_t axes = c.r2ax >> 8;
   if (!(axes & 512u)) {  // the ball may leave the array: check each coordinate
     const int cx = (int)(c.idx % (uint32_t)d.nx);
     const uint32_t t = c.idx / (uint32_t)d.nx;
@@ -809,52 +842,61 @@ __device__ __forceinline__ int owner_lane(int start, int k) {
 
 // One row-mode centre, one warp: the lanes take 32 rows (dz, dy) of the
 // ball at a time and compute each row's crescent spans (the row of the ball
-// minus the dominant neighbour's row, clamped to the array); then the spans'
-// voxels are shared out in order, so consecutive lanes update consecutive x.
-// Part p of `parts` takes the row steps p, p + parts, ...
+// minus the higher-ranked neighbours' rows, clamped to the array); then the
+// spans' voxels are shared out in order, so consecutive lanes update
+// consecutive x. Part p of `parts` takes the row steps p, p + parts, ...
 template <int NDIM>
 __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int parts, const Dims& d, size_t sy,
-                                                  size_t sz,
-                                                  bool touch, const uint32_t* __restrict__ dt2,
+                                                  size_t sz, bool touch, const uint32_t* __restrict__ dt2,
                                                   const uint32_t* __restrict__ labels,
-                                                  uint32_t* __restrict__ lt2, uint32_t& nupd) {
+                                                  uint32_t* __restrict__ lt2, const PaintLut& L, uint32_t& nupd) {
   const int lane = threadIdx.x & 31;
   const int side = 2 * c.R + 1, nrows = NDIM == 3 ? side * side : side;
   const int xmin = -c.cx, xmax = d.nx - 1 - c.cx;
-  for (int r0 = part * 32; r0 < nrows; r0 += 32 * parts) {
+  // the higher-ranked balls: dominant first, then the two extras (r^2 -1: none)
+  int hr[3], hx[3], hy[3], hz[3];
+  hr[0] = c.r2d, hx[0] = c.ddx, hy[0] = c.ddy, hz[0] = c.ddz;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int ec = c.eoff[q];
+    hr[q + 1] = c.er2[q], hx[q + 1] = ec % 3 - 1, hy[q + 1] = ec / 3 % 3 - 1, hz[q + 1] = ec / 9 - 1;
+  }
+  // row r = r0 + lane as (rq, rr) = (r / side, r % side) in 3D, advanced by
+  // the step without a division
+  const int step = 32 * parts;
+  int rq = 0, rr = 0, sq = 0, sr = 0;
+  if (NDIM == 3) {
+    rq = (part * 32 + lane) / side;
+    rr = part * 32 + lane - rq * side;
+    sq = step / side;
+    sr = step - sq * side;
+  }
+  for (int r0 = part * 32; r0 < nrows; r0 += step) {
     const int r = r0 + lane;
     int a1 = 0, n1 = 0, a2 = 0, n2 = 0, w = -1;  // spans [a1, a1 + n1), [a2, a2 + n2) of dx
     uint32_t rowbase = 0;                        // linear index of (cx, y, z)
     if (r < nrows) {
       int dz = 0, dy = r - c.R;  // 2D: one row per dy
       if (NDIM == 3) {
-        const int q = r / side;
-        dz = q - c.R;
-        dy = r - q * side - c.R;
+        dz = rq - c.R;
+        dy = rr - c.R;
       }
       const int z = c.cz + dz, y = c.cy + dy;
       const int h = (int)c.r2 - dz * dz - dy * dy;
       if (h >= 0 && z >= 0 && z < d.nz && y >= 0 && y < d.ny) {
-        w = (int)isqrt24((uint32_t)h);
-        // this row of the higher-ranked balls (dominant first, then the two
-        // extras) as one interval [elo, ehi] of dx: an extra's row joins
-        // only when it touches the interval so far (skipping one excludes
-        // less, which only paints more true-ball voxels)
+        w = isqrt_lut(L, h);
+        // this row of the higher-ranked balls as one interval [elo, ehi] of
+        // dx: an extra's row joins only when it touches the interval so far
+        // (skipping one excludes less, which only paints more true-ball
+        // voxels)
         int elo = 1, ehi = 0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          int rr, ox, oy, oz;
-          if (q == 0) {
-            rr = c.r2d, ox = c.ddx, oy = c.ddy, oz = c.ddz;
-          } else {
-            const int ec = c.eoff[q - 1];
-            rr = c.er2[q - 1], ox = ec % 3 - 1, oy = ec / 3 % 3 - 1, oz = ec / 9 - 1;
-          }
-          if (rr < 0) continue;
-          const int hd = rr - (dz - oz) * (dz - oz) - (dy - oy) * (dy - oy);
+          if (hr[q] < 0) continue;
+          const int hd = hr[q] - (dz - hz[q]) * (dz - hz[q]) - (dy - hy[q]) * (dy - hy[q]);
           if (hd < 0) continue;
-          const int wd = (int)isqrt24((uint32_t)hd);
-          const int lo = ox - wd, hi = ox + wd;
+          const int wd = isqrt_lut(L, hd);
+          const int lo = hx[q] - wd, hi = hx[q] + wd;
           if (elo > ehi) {
             elo = lo;
             ehi = hi;
@@ -877,6 +919,14 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int
         rowbase = (uint32_t)((size_t)z * sz + (size_t)y * sy + (size_t)c.cx);
       }
     }
+    if (NDIM == 3) {
+      rr += sr;
+      rq += sq;
+      if (rr >= side) {
+        rr -= side;
+        ++rq;
+      }
+    }
     int total;
     const int start = warp_starts(n1 + n2, lane, &total);
     for (int kb = 0; kb < total; kb += 32) {
@@ -897,67 +947,100 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int
   }
 }
 
-// Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
-// crescent voxels, two per lane in flight. A warp takes several chunks per
-// counter update when there is plenty of work (one hot counter serialises
-// its atomics), one at a time otherwise (so that small inputs still spread
-// over all warps).
-__device__ __forceinline__ uint32_t grab_size(uint32_t items, uint32_t most) {
-  const uint32_t warps = gridDim.x * (blockDim.x / 32);
-  return items >= 2u * most * warps ? most : 1u;
+// Up to two crescent voxels k0, k1 of table centres c0, c1: each is painted
+// unless it lies outside the array or in an extra ball, or on the sphere
+// and in the background, or (touch) carries another label.
+__device__ __forceinline__ void paint_tab_pair(const TabCentre& c0, int k0, bool v0, const TabCentre& c1, int k1,
+                                               bool v1, const Dims& d, bool touch,
+                                               const uint32_t* __restrict__ dt2,
+                                               const uint32_t* __restrict__ labels,
+                                               uint32_t* __restrict__ lt2, uint32_t& ntab) {
+  const uint32_t p0 = v0 ? g_cres_vox[c0.vstart + (uint32_t)k0] : 0u;
+  const uint32_t p1 = v1 ? g_cres_vox[c1.vstart + (uint32_t)k1] : 0u;
+  uint32_t i0 = 0, i1 = 0;
+  bool w0 = v0 && tab_voxel_index(c0, p0, d, i0);
+  bool w1 = v1 && tab_voxel_index(c1, p1, d, i1);
+  // inside the ball only the sphere |y|^2 == r^2 can be background
+  const uint32_t b0 = w0 && (p0 >> 24) ? dt2[i0] : 1u;
+  const uint32_t b1 = w1 && (p1 >> 24) ? dt2[i1] : 1u;
+  if (touch) {
+    w0 = w0 && labels[i0] == c0.label;
+    w1 = w1 && labels[i1] == c1.label;
+  }
+  if (w0 && b0) {
+    atomicMax(lt2 + i0, c0.r2ax & 0xFFu);
+    ++ntab;
+  }
+  if (w1 && b1) {
+    atomicMax(lt2 + i1, c1.r2ax & 0xFFu);
+    ++ntab;
+  }
 }
-constexpr uint32_t kChunkGrab = 4;  // chunks per counter update, at most
-constexpr uint32_t kBigGrab = 2;    // phase 1 centres per counter update, at most
+
+// Work items from one device counter by guided self-scheduling: a warp takes
+// about 1/(2 * warps) of the items not yet taken (at most `cap`), so the hot
+// counter sees few atomics while much work is left, and the last items still
+// spread over all warps one at a time.
+struct WorkGrab {
+  uint32_t next = 0, end = 0;
+  __device__ __forceinline__ bool take(unsigned int* ctr, uint32_t items, uint32_t cap, uint32_t& item) {
+    if (next == end) {
+      const uint32_t warps = gridDim.x * (blockDim.x / 32);
+      const uint32_t left = items > end ? items - end : 0u;  // end: the counter after this warp's last take
+      const uint32_t g = max(1u, min(cap, left / (2u * warps)));
+      uint32_t b = 0;
+      if ((threadIdx.x & 31) == 0) b = atomicAdd(ctr, g);
+      next = __shfl_sync(kFull, b, 0);
+      end = next + g;
+    }
+    if (next >= items) return false;
+    item = next++;
+    return true;
+  }
+};
+constexpr uint32_t kChunkGrab = 32;  // phase 2 chunks per counter update, at most
+constexpr uint32_t kBigGrab = 16;    // phase 1 centres per counter update, at most
+
+// Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
+// crescent voxels, two per lane in flight.
 __device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
                                                    size_t sy, size_t sz, bool touch,
                                                    const uint32_t* __restrict__ dt2,
                                                    const uint32_t* __restrict__ labels,
                                                    uint32_t* __restrict__ lt2, WsHeader* __restrict__ hdr,
-                                                   uint32_t& ntab) {
-  __shared__ TabCentre cs[8][32];
+                                                   const PaintLut& L, uint32_t& ntab) {
+  __shared__ uint4 csA[8][32], csB[8][32];  // (idx, vstart, start, r2ax), (S, ex) of the chunk's centres
+  __shared__ uint32_t csL[8][32];            // their labels (touch only)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t nchunks = (n + 31) / 32;
-  const uint32_t grab = grab_size(nchunks, kChunkGrab);
-  uint32_t ch = 0, grab_end = 0;
-  for (;;) {
-    if (ch == grab_end) {  // the next chunks from the shared counter
-      if (lane == 0) ch = atomicAdd(&hdr->ctr_small, grab);
-      ch = __shfl_sync(kFull, ch, 0);
-      grab_end = ch + grab;
-    }
-    if (ch >= nchunks) break;
-    const uint32_t i = ch++ * 32 + lane;
+  WorkGrab grab;
+  uint32_t ch = 0;
+  while (grab.take(&hdr->ctr_small, nchunks, kChunkGrab, ch)) {
+    const uint32_t i = ch * 32 + lane;
     int cnt = 0;
-    if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, cs[w][lane]);
+    TabCentre mine;
+    if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, L, mine);
     int total;
     const int start = warp_starts(cnt, lane, &total);
-    if (i < n) cs[w][lane].start = start;
+    if (i < n) {
+      csA[w][lane] = make_uint4(mine.idx, mine.vstart, (uint32_t)start, mine.r2ax);
+      csB[w][lane] = make_uint4((uint32_t)mine.S[0], (uint32_t)mine.S[1], (uint32_t)mine.S[2], mine.ex);
+      csL[w][lane] = mine.label;
+    }
     __syncwarp();
+    auto load = [&](int j) {
+      TabCentre c;
+      const uint4 A = csA[w][j], B = csB[w][j];
+      c.idx = A.x, c.vstart = A.y, c.start = A.z, c.r2ax = A.w;
+      c.S[0] = (int)B.x, c.S[1] = (int)B.y, c.S[2] = (int)B.z, c.ex = B.w;
+      c.label = touch ? csL[w][j] : 0u;
+      return c;
+    };
     for (int kb = 0; kb < total; kb += 64) {
       const int k0 = kb + lane, k1 = k0 + 32;
-      const int j0 = owner_lane(start, k0), j1 = owner_lane(start, k1);
-      const TabCentre& c0 = cs[w][j0];
-      const TabCentre& c1 = cs[w][j1];
-      const uint32_t p0 = k0 < total ? g_cres_vox[c0.vstart + (uint32_t)(k0 - c0.start)] : 0u;
-      const uint32_t p1 = k1 < total ? g_cres_vox[c1.vstart + (uint32_t)(k1 - c1.start)] : 0u;
-      uint32_t i0 = 0, i1 = 0;
-      bool w0 = k0 < total && tab_voxel_index(c0, p0, d, i0);
-      bool w1 = k1 < total && tab_voxel_index(c1, p1, d, i1);
-      // inside the ball only the sphere |y|^2 == r^2 can be background
-      const uint32_t b0 = w0 && (p0 >> 24) ? dt2[i0] : 1u;
-      const uint32_t b1 = w1 && (p1 >> 24) ? dt2[i1] : 1u;
-      if (touch) {
-        w0 = w0 && labels[i0] == c0.label;
-        w1 = w1 && labels[i1] == c1.label;
-      }
-      if (w0 && b0) {
-        atomicMax(lt2 + i0, c0.r2);
-        ++ntab;
-      }
-      if (w1 && b1) {
-        atomicMax(lt2 + i1, c1.r2);
-        ++ntab;
-      }
+      const TabCentre c0 = load(owner_lane(start, k0)), c1 = load(owner_lane(start, k1));
+      paint_tab_pair(c0, k0 - (int)c0.start, k0 < total, c1, k1 - (int)c1.start, k1 < total, d, touch, dt2, labels,
+                     lt2, ntab);
     }
     __syncwarp();
   }
@@ -974,11 +1057,9 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
   __shared__ Centre cs[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t nchunks = (n + 31) / 32;
-  for (;;) {
-    uint32_t ch = 0;
-    if (lane == 0) ch = atomicAdd(&hdr->ctr_small, 1u);
-    ch = __shfl_sync(kFull, ch, 0);
-    if (ch >= nchunks) break;
+  WorkGrab grab;
+  uint32_t ch = 0;
+  while (grab.take(&hdr->ctr_small, nchunks, kChunkGrab, ch)) {
     const uint32_t i = ch * 32 + lane;
     int cnt = 0;
     if (i < n) cnt = make_centre<2>(surv[i], d, sy, sz, touch, dt2, labels, cs[w][lane]);
@@ -1007,7 +1088,7 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
 //    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
 //    and small crescents balance.
 template <int NDIM>
-__global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__ surv,
+__global__ void __launch_bounds__(256, 5) lt_paint_kernel(const uint4* __restrict__ surv,
                                                        const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
@@ -1018,39 +1099,29 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   const bool touch = *(volatile uint32_t*)&hdr->touch != 0;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   uint32_t nupd = 0, ntab = 0;  // updates this thread issued: row by row, from tables
+  __shared__ PaintLut lut;
+  init_paint_lut(lut);
+  __syncthreads();
   {
-    const uint32_t grab = grab_size(nbig, kBigGrab);
-    uint32_t b = 0, grab_end = 0;
-    for (;;) {
-      if (b == grab_end) {  // the next records from the shared counter
-        if (lane == 0) b = atomicAdd(&hdr->ctr_big, grab);
-        b = __shfl_sync(kFull, b, 0);
-        grab_end = b + grab;
-      }
-      if (b >= nbig) break;
-      const uint4 rec = surv[record_capacity(d.n) - 1 - b++];
+    WorkGrab grab;
+    uint32_t b = 0;
+    while (grab.take(&hdr->ctr_big, nbig, kBigGrab, b)) {
+      const uint4 rec = surv[record_capacity(d.n) - 1 - b];
       if (NDIM == 3 && (rec.z & kTableRecord)) {
         TabCentre c;
-        const int items = make_tab_centre(rec, sy, sz, touch, labels, c);
-        for (int k = lane; k < items; k += 32) {
-          const uint32_t p = g_cres_vox[c.vstart + (uint32_t)k];
-          uint32_t i = 0;
-          if (!tab_voxel_index(c, p, d, i)) continue;
-          if ((p >> 24) && dt2[i] == 0) continue;  // only the sphere can be background
-          if (touch && labels[i] != c.label) continue;
-          atomicMax(lt2 + i, c.r2);
-          ++ntab;
-        }
+        const int items = make_tab_centre(rec, sy, sz, touch, labels, lut, c);
+        for (int k = lane; k < items; k += 64)
+          paint_tab_pair(c, k, true, c, k + 32, k + 32 < items, d, touch, dt2, labels, lt2, ntab);
       } else {
         Centre c;
         make_centre<NDIM>(rec, d, sy, sz, touch, dt2, labels, c);
         paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFu), max(1, (int)(rec.w >> 8)), d, sy, sz, touch, dt2,
-                                labels, lt2, nupd);
+                                labels, lt2, lut, nupd);
       }
     }
   }
   if (NDIM == 3)
-    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, ntab);
+    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, lut, ntab);
   else
     paint_row_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, nupd);
 #pragma unroll
@@ -1098,7 +1169,12 @@ bool make_tensor_map_u32_3d(CUtensorMap* map, const void* base, int nx, int ny, 
 
 size_t lt_workspace_bytes(const Dims& d) { return align_up(record_capacity(d.n) * sizeof(uint4)); }
 
-cudaError_t lt_prepare_device() { return ensure_tables(); }
+int paint_fit(int ndim);
+
+cudaError_t lt_prepare_device() {
+  paint_fit(3);
+  return ensure_tables();
+}
 
 // Timeout self-test: the TMA ridge kernel on a 32 x 8 x 8 all-background
 // volume carved from `ws`, with every plane barrier expecting 16 bytes more
@@ -1172,10 +1248,31 @@ cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_
   return cudaGetLastError();
 }
 
+// CTAs of the paint kernel that fit on one SM (queried once; callers that
+// capture graphs query it first through lt_prepare_device)
+int paint_fit(int ndim) {
+  static const int fit[2] = {[] {
+                               int v = 0;
+                               if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lt_paint_kernel<2>, 256, 0) !=
+                                       cudaSuccess || v < 1)
+                                 v = 1;
+                               return v;
+                             }(),
+                             [] {
+                               int v = 0;
+                               if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lt_paint_kernel<3>, 256, 0) !=
+                                       cudaSuccess || v < 1)
+                                 v = 1;
+                               return v;
+                             }()};
+  return fit[ndim == 3];
+}
+
 cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                             WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu) {
   const uint4* surv = reinterpret_cast<const uint4*>(body);
-  const int bps = tu.paint_blocks_per_sm > 0 ? tu.paint_blocks_per_sm : 8;
+  // the persistent grid: the tuned CTAs per SM, at most as many as fit
+  const int bps = std::min(tu.paint_blocks_per_sm > 0 ? tu.paint_blocks_per_sm : 8, paint_fit(d.ndim));
   const unsigned pblocks = (unsigned)(sm_count() * bps);
   {
     TraceScope t("lt_paint", s);
