@@ -450,12 +450,6 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       const int c = (ty + 1) * kBX + (tx + kOX);
       const uint32_t r2 = D0[c];
       const uint32_t kmax[3] = {kq.y, kq.z, kq.w};
-      int m[3] = {kNoTable, kNoTable, kNoTable};
-      if (r2 <= kMCap) {
-        m[0] = (int)mt[r2];
-        m[1] = (int)mt[(kMCap + 1) + r2];
-        if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
-      }
       int brn[3] = {-1, -1, -1};
       uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
 #pragma unroll
@@ -487,6 +481,12 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           }
         } else {
           // the candidate whose ball comes closest to containing c's
+          int m[3] = {kNoTable, kNoTable, kNoTable};
+          if (r2 <= kMCap) {
+            m[0] = (int)mt[r2];
+            m[1] = (int)mt[(kMCap + 1) + r2];
+            if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
+          }
           int best = INT_MIN;
 #pragma unroll
           for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
@@ -508,9 +508,13 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           }
         const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
         if (NDIM == 3 && tab) {
-          const int R = (int)isqrt24(r2);
+          // the ball inside the array: R <= x, x + R < nx per axis, R =
+          // floor(sqrt(r^2)); R <= k exactly when r^2 < (k + 1)^2
           const int x = x0 + tx, y = y0 + ty;
-          const uint32_t inside = x >= R && x + R < d.nx && y >= R && y + R < d.ny && z >= R && z + R < d.nz;
+          auto fits = [&](int v, int nv) {
+            return (int64_t)r2 < (int64_t)(v + 1) * (v + 1) && (int64_t)r2 < (int64_t)(nv - v) * (nv - v);
+          };
+          const uint32_t inside = fits(x, d.nx) && fits(y, d.ny) && fits(z, d.nz);
           rec = make_uint4(v, vstart | (best << 22),
                            r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord, er);
         } else {
@@ -998,8 +1002,8 @@ struct WorkGrab {
     return true;
   }
 };
-constexpr uint32_t kChunkGrab = 32;  // phase 2 chunks per counter update, at most
-constexpr uint32_t kBigGrab = 16;    // phase 1 centres per counter update, at most
+constexpr uint32_t kChunkGrab = 8;  // phase 2 chunks per counter update, at most
+constexpr uint32_t kBigGrab = 8;    // phase 1 centres per counter update, at most
 
 // Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
 // crescent voxels, two per lane in flight.
