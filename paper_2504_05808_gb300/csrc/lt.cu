@@ -28,11 +28,11 @@
 // signed permutation of the axes maps it onto the crescent of the canonical
 // offset of d's class, (1,0,0), (1,1,0) or (1,1,1). A kept centre has
 // r_c^2 <= r_D^2 < M(d, r_c^2), about 2 |d| r_c values of r_D^2, so for
-// r_c^2 <= 144 every crescent fits a table of 1.4 M voxel offsets. Such a
+// r_c^2 <= 200 every crescent fits a table of 3.1 M voxel offsets. Such a
 // centre paints its tabulated crescent voxel by voxel (lanes of a warp share
 // the voxels of 32 centres). The dominant neighbour D is the one whose
 // crescent is smallest (for larger radii: the one whose ball comes closest to
-// containing c's). Centres with r^2 > 144, without a higher-ranked neighbour,
+// containing c's). Centres with r^2 > 200, without a higher-ranked neighbour,
 // or in 2D paint row by row instead.
 //
 // Voxels strictly inside B(c) are foreground (DT2(c) is the distance to the
@@ -44,7 +44,7 @@
 // the label test is skipped.
 //
 // The tables are built once per process on the host and copied once per
-// device into the arrays below (about 13 MiB of device memory).
+// device into the arrays below (about 23 MiB of device memory).
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -61,9 +61,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kMCap = 1u << 18;  // containment table covers r^2 <= 2^18
-constexpr int kCresT = 144;           // crescent tables cover r^2 <= 144
-constexpr int kCresMaxCombos = 12288;
-constexpr int kCresMaxVoxels = 2304 * 1024;  // both orderings (about 2.16 M voxels)
+constexpr int kCresT = 200;           // crescent tables cover r^2 <= 200
+constexpr int kCresMaxCombos = 16384;
+constexpr int kCresMaxVoxels = 5 * 1024 * 1024;  // both orderings (about 4.8 M voxels)
 constexpr uint32_t kNoDominant = 31u;
 constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a crescent table
 constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
@@ -80,9 +80,9 @@ constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
 __device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
 __device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
-// per combination: x = first voxel | size << 22, y = first voxel of the same
-// crescent in the alternative order below
-__device__ uint2 g_cres_combo[kCresMaxCombos];
+// per combination: x = first voxel, y = first voxel of the same crescent in
+// the alternative order below, z = size
+__device__ uint4 g_cres_combo[kCresMaxCombos];
 // (the same crescents with another canonical axis innermost: y for class 1,
 // z for class 2; class 3 has one order)
 // canonical crescent voxels: (x+128) | (y+128) << 8 | (z+128) << 16 |
@@ -92,7 +92,7 @@ __device__ uint32_t g_cres_vox[kCresMaxVoxels];
 // ------------------------------------------------------------ host tables
 struct HostTables {
   std::vector<uint32_t> m3, m2, base, start, start_alt, vox;
-  std::vector<uint2> combo;
+  std::vector<uint4> combo;
   bool ok = false;
 };
 
@@ -175,11 +175,12 @@ HostTables* build_host_tables() {
       }
     }
   t->ok = t->start.size() <= (size_t)kCresMaxCombos + 1 && t->vox.size() <= (size_t)kCresMaxVoxels;
-  // table records hold a crescent's first voxel in 22 bits and its size in 10
-  for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 1024u;
-  t->ok = t->ok && t->vox.size() < (1u << 22);
+  // table records hold a crescent's size in 11 bits; the ridge kernel keeps
+  // the first combination of each (class, r^2) in 16 bits
+  for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 2048u;
+  t->ok = t->ok && t->start.size() < (1u << 16);
   for (size_t i = 0; i + 1 < t->start.size(); ++i)
-    t->combo.push_back(make_uint2(t->start[i] | ((t->start[i + 1] - t->start[i]) << 22), t->start_alt[i]));
+    t->combo.push_back(make_uint4(t->start[i], t->start_alt[i], t->start[i + 1] - t->start[i], 0u));
   return t;
 }
 
@@ -201,13 +202,13 @@ cudaError_t ensure_tables() {
   e = cudaMemcpyToSymbol(g_m3, h.m3.data(), h.m3.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_m2, h.m2.data(), h.m2.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_base, h.base.data(), h.base.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_combo, h.combo.data(), h.combo.size() * sizeof(uint2));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_combo, h.combo.data(), h.combo.size() * sizeof(uint4));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_vox, h.vox.data(), h.vox.size() * 4);
   if (e == cudaSuccess) g_tables_on[dev] = true;
   return e;
 }
 
-__device__ __forceinline__ uint32_t cres_combo(const uint32_t* base, int cls, uint32_t r2, uint32_t rd2) {
+__device__ __forceinline__ uint32_t cres_combo(const uint16_t* base, int cls, uint32_t r2, uint32_t rd2) {
   return base[cls * (kCresT + 1) + r2] + (rd2 - r2);
 }
 
@@ -235,11 +236,11 @@ __device__ __forceinline__ uint32_t cres_combo(const uint32_t* base, int cls, ui
 // 2D centre. The back gets those a warp paints alone: bigger crescents and
 // the centres painted row by row.
 // Records (uint4). Offset codes: (dz+1)*9 + (dy+1)*3 + (dx+1), 31 for none.
-//   Table centres (3D): x = linear index; y = first crescent voxel | crescent
-//   size << 22; z = r^2 | dominant code << 8 | codes of up to two more
-//   higher-ranked same-label neighbours << 13 (5 bits each) | ball inside
-//   the array << 23 | kTableRecord; w = those two neighbours' r^2 (8 bits
-//   each, 0xFF none).
+//   Table centres (3D): x = linear index; y = first crescent voxel; z = r^2 |
+//   dominant code << 8 | codes of up to two more higher-ranked same-label
+//   neighbours << 13 (5 bits each) | ball inside the array << 23 |
+//   kTableRecord; w = those two neighbours' r^2 (8 bits each, 0xFF none) |
+//   crescent size << 16.
 //   Painting needs no other lookup.
 //   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
 //   z = the two extra codes; w = part | parts << 8 (row-mode centres go to
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   __shared__ __align__(8) uint64_t bar[kSlots];
   __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s, nkept_s;
   __shared__ uint4 keptq[256];  // pass 2a -> 2b: tile position, per-class best keys
-  __shared__ uint32_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 1];  // copy of g_cres_base
+  __shared__ uint16_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 2];  // copy of g_cres_base
   const int tid = threadIdx.x, lane = tid & 31;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int z0 = NDIM == 3 ? blockIdx.z * RZ + z_base : 0;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
     }
   };
   if (NDIM == 3)
-    for (int i = tid; i < 3 * (kCresT + 1); i += 256) sbase[i] = g_cres_base[i];
+    for (int i = tid; i < 3 * (kCresT + 1); i += 256) sbase[i] = (uint16_t)g_cres_base[i];
   if (tid == 0) {
     cntA = cntB = 0;
     // after a timeout anywhere in this launch, the remaining CTAs stop at once
@@ -465,16 +466,17 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           // the candidate whose crescent has the fewest voxels; its voxels
           // in the order with world x innermost (the alternative order when
           // the offset has no x component)
-          uint2 ce[3];
+          uint4 ce[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k)
-            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(~0u, 0u);
+            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])]
+                                : make_uint4(0u, 0u, UINT_MAX, 0u);
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            const uint32_t sz = ce[k].x >> 22;
+            const uint32_t sz = ce[k].z;
             if (brn[k] >= 0 && sz < best) {
               best = sz;
-              vstart = bcode[k] % 3 == 1 ? ce[k].y : ce[k].x & 0x3FFFFFu;
+              vstart = bcode[k] % 3 == 1 ? ce[k].y : ce[k].x;
               code = bcode[k];
               kd = k;
             }
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
         }
         const uint32_t v = (uint32_t)((size_t)z * plane + (size_t)(y0 + ty) * d.nx + (x0 + tx));
         // the other classes' candidates: extra balls a crescent voxel may lie
-        // in, with their r^2 (below M(d, r^2) <= 188 for table centres)
+        // in, with their r^2 (below M(d, r^2) <= 252 for table centres)
         uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0xFFFFu, ne = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -515,8 +517,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
             return (int64_t)r2 < (int64_t)(v + 1) * (v + 1) && (int64_t)r2 < (int64_t)(nv - v) * (nv - v);
           };
           const uint32_t inside = fits(x, d.nx) && fits(y, d.ny) && fits(z, d.nz);
-          rec = make_uint4(v, vstart | (best << 22),
-                           r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord, er);
+          rec = make_uint4(v, vstart, r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord,
+                           er | (best << 16));
         } else {
           rec = make_uint4(v, r2 | (code << 25), extra, 0u);
         }
@@ -745,7 +747,7 @@ __device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, 
                                                const uint32_t* __restrict__ labels, const PaintLut& L,
                                                TabCentre& c) {
   c.idx = rec.x;
-  c.vstart = rec.y & 0x3FFFFFu;
+  c.vstart = rec.y;
   c.start = 0;
   const uint32_t code = (rec.z >> 8) & 31u;
   const uint32_t pm = L.perm[code];
@@ -771,7 +773,7 @@ __device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, 
   }
   c.ex = ex;
   c.label = touch ? labels[c.idx] : 0u;
-  return (int)(rec.y >> 22);
+  return (int)((rec.w >> 16) & 0x7FFu);
 }
 
 // Linear index of canonical crescent voxel p of c; false when the voxel lies

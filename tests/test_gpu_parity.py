@@ -255,3 +255,24 @@ def test_repeated_calls_reuse_workspace(lt):
         _, _, S_ref, R_ref = oracle.pipeline(m, l, 64)
         assert_close(S.cpu().numpy(), S_ref, "S")
         assert_close(R.cpu().numpy(), R_ref, "R")
+
+
+def test_crescent_table_bounds(lt):
+    """Rotated ellipsoids whose inscribed-ball radii run across the edge of
+    the tabulated crescents (r^2 = 200): kept centres on both sides of it,
+    painted from tables and row by row, next to each other in one object."""
+    rng = np.random.default_rng(7)
+    for axes in [(14.5, 17.0, 18.0), (14.3, 16.5, 22.0), (14.9, 14.9, 25.0)]:
+        n = int(2 * max(axes)) + 5
+        g = np.indices((n, n, n)).reshape(3, -1).T - (n - 1) / 2.0
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        rot = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+        u = g @ rot
+        mask = (((u / np.array(axes)) ** 2).sum(1) <= 1.0).reshape(n, n, n).astype(np.uint8)
+        d, _ = check_full(lt, mask, mask.astype(np.uint32), 2)
+        r2 = d[mask > 0]
+        assert r2.max() > 200 and np.count_nonzero((r2 > 144) & (r2 <= 200)) > 0
