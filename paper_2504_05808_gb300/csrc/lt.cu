@@ -80,9 +80,9 @@ constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
 __device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
 __device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
-// per combination: x = first voxel, y = first voxel of the same crescent in
-// the alternative order below, z = size
-__device__ uint4 g_cres_combo[kCresMaxCombos];
+// per combination: x = first voxel | (size & 511) << 23, y = first voxel of
+// the same crescent in the alternative order below | (size >> 9) << 23
+__device__ uint2 g_cres_combo[kCresMaxCombos];
 // (the same crescents with another canonical axis innermost: y for class 1,
 // z for class 2; class 3 has one order)
 // canonical crescent voxels: (x+128) | (y+128) << 8 | (z+128) << 16 |
@@ -92,7 +92,7 @@ __device__ uint32_t g_cres_vox[kCresMaxVoxels];
 // ------------------------------------------------------------ host tables
 struct HostTables {
   std::vector<uint32_t> m3, m2, base, start, start_alt, vox;
-  std::vector<uint4> combo;
+  std::vector<uint2> combo;
   bool ok = false;
 };
 
@@ -178,9 +178,11 @@ HostTables* build_host_tables() {
   // table records hold a crescent's size in 11 bits; the ridge kernel keeps
   // the first combination of each (class, r^2) in 16 bits
   for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 2048u;
-  t->ok = t->ok && t->start.size() < (1u << 16);
-  for (size_t i = 0; i + 1 < t->start.size(); ++i)
-    t->combo.push_back(make_uint4(t->start[i], t->start_alt[i], t->start[i + 1] - t->start[i], 0u));
+  t->ok = t->ok && t->start.size() < (1u << 16) && t->vox.size() < (1u << 23);
+  for (size_t i = 0; i + 1 < t->start.size(); ++i) {
+    const uint32_t size = t->start[i + 1] - t->start[i];
+    t->combo.push_back(make_uint2(t->start[i] | ((size & 511u) << 23), t->start_alt[i] | ((size >> 9) << 23)));
+  }
   return t;
 }
 
@@ -202,7 +204,7 @@ cudaError_t ensure_tables() {
   e = cudaMemcpyToSymbol(g_m3, h.m3.data(), h.m3.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_m2, h.m2.data(), h.m2.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_base, h.base.data(), h.base.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_combo, h.combo.data(), h.combo.size() * sizeof(uint4));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_combo, h.combo.data(), h.combo.size() * sizeof(uint2));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cres_vox, h.vox.data(), h.vox.size() * 4);
   if (e == cudaSuccess) g_tables_on[dev] = true;
   return e;
@@ -466,17 +468,16 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           // the candidate whose crescent has the fewest voxels; its voxels
           // in the order with world x innermost (the alternative order when
           // the offset has no x component)
-          uint4 ce[3];
+          uint2 ce[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k)
-            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])]
-                                : make_uint4(0u, 0u, UINT_MAX, 0u);
+            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(0u, 0u);
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            const uint32_t sz = ce[k].z;
+            const uint32_t sz = (ce[k].x >> 23) | ((ce[k].y >> 23) << 9);
             if (brn[k] >= 0 && sz < best) {
               best = sz;
-              vstart = bcode[k] % 3 == 1 ? ce[k].y : ce[k].x;
+              vstart = (bcode[k] % 3 == 1 ? ce[k].y : ce[k].x) & 0x7FFFFFu;
               code = bcode[k];
               kd = k;
             }
