@@ -288,10 +288,11 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   const size_t plane = (size_t)d.nx * d.ny;
   const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
   const unsigned below = (1u << lane) - 1u;
-  // plane p lives in slot (p - z0 + 1) mod 4; its copy is the k-th into that
-  // slot, k = (p - z0 + 1) / 4, completing the barrier phase of parity k & 1
-  auto slot_of = [&](int p) { return (p - z0 + 1) & (kSlots - 1); };
-  auto parity_of = [&](int p) { return (uint32_t)(((p - z0 + 1) >> 2) & 1); };
+  // plane p lives in slot (p - z0 + 1) mod kSlots; its copy is the k-th into
+  // that slot, k = (p - z0 + 1) / kSlots, completing the barrier phase of
+  // parity k & 1
+  auto slot_of = [&](int p) { return (int)((uint32_t)(p - z0 + 1) % kSlots); };
+  auto parity_of = [&](int p) { return ((uint32_t)(p - z0 + 1) / kSlots) & 1u; };
   auto issue = [&](int p) {
     const int s = slot_of(p);
     mbar_expect_tx(&bar[s], 2 * kPlaneBytes + wt.extra_tx);
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   if (flags & 4u) return;
   if (TMA) {
     if (tid == 0)
-      for (int p = z0 - 1; p <= min(z1, z0 + 2); ++p) issue(p);
+      for (int p = z0 - 1; p <= min(z1, z0 + kSlots - 2); ++p) issue(p);
   } else if (NDIM == 3) {
     load_plane(z0 - 1);
     load_plane(z0);
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       // bounded) for the copies this CTA still has in flight, and stop
       if (tid == 0) {
         atomicOr(&hdr->error, ERR_TIMEOUT);
-        for (int p = z - 1; p <= min(z1, z + 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p), wt.limit_ns);
+        for (int p = z - 1; p <= min(z1, z + kSlots - 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p), wt.limit_ns);
       }
       return;
     }
@@ -557,9 +558,9 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       if (keepB) buf[kListBuf - 1 - (wb + __popc(bb & below))] = rec;
     }
     __syncthreads();  // plane z-1 is free again; the buffer may be flushed
-    if (TMA && tid == 0 && z + 3 <= z1) {
+    if (TMA && tid == 0 && z + kSlots - 1 <= z1) {
       fence_proxy_async();
-      issue(z + 3);
+      issue(z + kSlots - 1);
     }
     if (tid == 0) nwork_s = nkept_s = 0;
     if (cntA + cntB > kListBuf - 256 || z + 1 == z1) {  // uniform: read after the barrier
