@@ -276,3 +276,26 @@ def test_crescent_table_bounds(lt):
         d, _ = check_full(lt, mask, mask.astype(np.uint32), 2)
         r2 = d[mask > 0]
         assert r2.max() > 200 and np.count_nonzero((r2 > 144) & (r2 <= 200)) > 0
+
+
+@pytest.mark.parametrize("shape", [(64, 80), (64, 81), (4, 16, 80)])
+def test_fixed_point_lt_of_every_small_value(lt, shape):
+    """Each voxel its own object with LT2 = 1, 2, ...: the per-object LT sum
+    is exactly round(sqrtf(LT2) * 2^20) (float32 square root, rounding half
+    to even), for the tabulated small values and the computed larger ones,
+    in the four-voxel (nx % 4 == 0) and the one-voxel reduction."""
+    import torch
+    n = int(np.prod(shape))
+    t = np.arange(1, n + 1, dtype=np.uint32).reshape(shape)
+    labels = t.copy()
+    S = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    R = torch.empty_like(S)
+    stats = {k: torch.empty(n + 1, dtype=torch.int32, device="cuda") for k in ("volume", "n_shell", "max_lt2")}
+    stats.update({k: torch.empty(n + 1, dtype=torch.int64, device="cuda") for k in ("sum_lt", "sum_shell_lt")})
+    ws = lt.lt_shape_measures(dev_u32(labels), dev_u32(t), n + 1, S, R, stats)
+    lt.lt_workspace_status(ws)
+    want = np.rint(np.sqrt(np.arange(1, n + 1, dtype=np.float32)) * np.float32(2.0 ** 20)).astype(np.int64)
+    got = stats["sum_lt"].cpu().numpy()[1:]
+    assert np.array_equal(got, want)
+    assert np.array_equal(stats["sum_shell_lt"].cpu().numpy()[1:], want)  # every one-voxel object is shell
+    assert np.array_equal(stats["max_lt2"].cpu().numpy()[1:], np.arange(1, n + 1))
