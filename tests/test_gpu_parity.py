@@ -215,16 +215,26 @@ def test_device_detected_errors(lt):
 
 def test_host_buffer_entry_matches_device_path(lt):
     """The host-buffer entry copies in z-slabs and runs the ridge pass slab by
-    slab as the labels land; it must give the device path's bits, also for
-    slab counts that do not divide the volume and in 2D."""
+    slab as the labels land; it must give the device path's bits: for slab
+    counts that do not divide the volume, in 2D, with touching labels
+    (painting then tests labels), and with a ball thicker than the thinnest
+    slab."""
     import torch
     import scipy.ndimage as ndi
     rng = np.random.default_rng(8)
     f = ndi.gaussian_filter(rng.random((70, 45, 36)), 2.0)
     rag = (f > np.quantile(f, 0.5)).astype(np.uint8)
     rag_l = ndi.label(rag)[0].astype(np.uint32)
+    m2, l2, n2 = synth.workload("ellipsoids_3d_128", 2)
+    touch = l2.copy()
+    half = (np.indices(l2.shape)[2] >= 64) & (l2 > 0)
+    touch[half] += np.uint32(n2)  # halves of objects cut at x = 64 touch their other half
+    g = np.indices((100, 40, 40)) - np.array([50, 20, 20]).reshape(3, 1, 1, 1)
+    big = ((g ** 2).sum(0) <= 12 ** 2).astype(np.uint8)  # radius 12 > the 4-plane last slab
+    big[5:9, 3:7, 3:7] = 1
+    big_l = ndi.label(big)[0].astype(np.uint32)
     cases = [synth.workload("ellipsoids_3d_128", 1), synth.workload("ellipses_2d_256", 2),
-             (rag, rag_l, int(rag_l.max()) + 1)]
+             (rag, rag_l, int(rag_l.max()) + 1), (m2, touch, 2 * n2), (big, big_l, int(big_l.max()) + 1)]
     for m, l, n in cases:
         _, _, S_dev, R_dev, _ = gpu_pipeline(lt, m, l, n)
         mh = torch.from_numpy(m).pin_memory()
