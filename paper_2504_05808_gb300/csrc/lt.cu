@@ -136,7 +136,12 @@ HostTables* build_host_tables() {
   // (class 2) innermost, the axis that is world x when the offset has no x
   // component, so that consecutive voxels run along memory rows
   const int dl[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 1, 1}};
-  auto crescent = [&](int k, int r2, uint32_t rd2, int inner) {
+  // the lattice points of B(0, r^2) in the order with axis `inner` running
+  // fastest, each with its squared distance to the class-k offset; a
+  // crescent is the ordered subsequence with that distance above rd^2
+  std::vector<std::pair<uint32_t, int>> pts;
+  auto ball = [&](int k, int r2, int inner) {
+    pts.clear();
     const int Rr = isqrt_host(r2);
     for (int u = -Rr; u <= Rr; ++u)
       for (int v = -Rr; v <= Rr; ++v)
@@ -149,19 +154,24 @@ HostTables* build_host_tables() {
           if (n > r2) continue;
           const int e = (c[0] - dl[k][0]) * (c[0] - dl[k][0]) + (c[1] - dl[k][1]) * (c[1] - dl[k][1]) +
                         (c[2] - dl[k][2]) * (c[2] - dl[k][2]);
-          if (e <= (int)rd2) continue;
-          t->vox.push_back((uint32_t)(c[0] + 128) | ((uint32_t)(c[1] + 128) << 8) |
-                           ((uint32_t)(c[2] + 128) << 16) | ((n == r2 ? 1u : 0u) << 24));
+          pts.emplace_back((uint32_t)(c[0] + 128) | ((uint32_t)(c[1] + 128) << 8) |
+                               ((uint32_t)(c[2] + 128) << 16) | ((n == r2 ? 1u : 0u) << 24),
+                           e);
         }
+  };
+  auto crescent = [&](uint32_t rd2) {
+    for (const auto& p : pts)
+      if (p.second > (int)rd2) t->vox.push_back(p.first);
   };
   t->base.assign(3 * (kCresT + 1), 0u);
   for (int k = 0; k < 3; ++k)
     for (int r2 = 0; r2 <= kCresT; ++r2) {
       t->base[k * (kCresT + 1) + r2] = (uint32_t)t->start.size();
       const uint32_t mlim = t->m3[k * (size_t)(cap + 1) + r2];
+      ball(k, r2, 0);
       for (uint32_t rd2 = (uint32_t)r2; rd2 < mlim; ++rd2) {
         t->start.push_back((uint32_t)t->vox.size());
-        crescent(k, r2, rd2, 0);
+        crescent(rd2);
       }
     }
   t->start.push_back((uint32_t)t->vox.size());  // end of the last crescent
@@ -169,9 +179,10 @@ HostTables* build_host_tables() {
   for (int k = 0; k < 2; ++k)
     for (int r2 = 0; r2 <= kCresT; ++r2) {
       const uint32_t mlim = t->m3[k * (size_t)(cap + 1) + r2];
+      ball(k, r2, k == 0 ? 1 : 2);
       for (uint32_t rd2 = (uint32_t)r2; rd2 < mlim; ++rd2) {
         t->start_alt[t->base[k * (kCresT + 1) + r2] + (rd2 - r2)] = (uint32_t)t->vox.size();
-        crescent(k, r2, rd2, k == 0 ? 1 : 2);
+        crescent(rd2);
       }
     }
   t->ok = t->start.size() <= (size_t)kCresMaxCombos + 1 && t->vox.size() <= (size_t)kCresMaxVoxels;
