@@ -126,7 +126,7 @@ def algorithmic_bytes(name, n, n_surv):
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read
 # and _write, one pass) of the current kernels on the 512^3 particle volume;
 # valid for that workload only.
-TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344350000, "edt_cols_y": 751890000, "edt_cols_z": 1014730000, "lt_ridge": 1758320000, "lt_paint": 1892820000, "shape_reduce": 848899020}}
+TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344030000, "edt_cols_y": 751630000, "edt_cols_z": 1014850000, "lt_ridge": 1758380000, "lt_paint": 1736060000, "shape_reduce": 849004500}}
 
 
 def update_rate_probe(lt, dev):

@@ -1107,7 +1107,7 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
 //    chunk's work items (crescent voxels in 3D, row segments in 2D), so big
 //    and small crescents balance.
 template <int NDIM>
-__global__ void __launch_bounds__(256, 5) lt_paint_kernel(const uint4* __restrict__ surv,
+__global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__ surv,
                                                        const uint32_t* __restrict__ dt2,
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
