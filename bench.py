@@ -126,7 +126,7 @@ def algorithmic_bytes(name, n, n_surv):
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read
 # and _write, one pass) of the current kernels on the 512^3 particle volume;
 # valid for that workload only.
-TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344030000, "edt_cols_y": 751630000, "edt_cols_z": 1014850000, "lt_ridge": 1758380000, "lt_paint": 1736060000, "shape_reduce": 849004500}}
+TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344270000, "edt_cols_y": 751800000, "edt_cols_z": 1009210000, "lt_ridge": 1758240000, "lt_paint": 1734620000, "shape_reduce": 848861390}}
 
 
 def update_rate_probe(lt, dev):

@@ -184,14 +184,20 @@ __device__ __forceinline__ uint32_t load1(const uint32_t* src) { return *src; }
 // (length L, stride sp between elements); blockIdx.y picks the other
 // coordinate (stride so). `in` and `out` have the same layout and may be the
 // same array (the tile is read completely before anything is written).
+// Threads per CTA of a column tile of width TX: 512 for 32-column tiles
+// (their rows are whole 128-byte lines; three such CTAs fit an SM), else 256.
+template <int TX>
+__host__ __device__ constexpr int cols_threads() { return TX == 32 ? 512 : 256; }
+
 template <int TX, typename In>
-__global__ void __launch_bounds__(256) edt_cols_kernel(const In* in, uint32_t* out, int L, size_t sp,
-                                                       int nx, size_t so, int vec) {
+__global__ void __launch_bounds__(cols_threads<TX>()) edt_cols_kernel(const In* in, uint32_t* out, int L,
+                                                                      size_t sp, int nx, size_t so, int vec) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* tile = reinterpret_cast<uint32_t*>(smem_raw);
-  constexpr int Q = TX / 4;           // 4-element pieces per tile row
-  constexpr int kRows = 256 / Q;      // tile rows loaded per sweep of the CTA
-  constexpr int kOutRows = 256 / TX;  // tile rows computed per sweep
+  constexpr int NT = cols_threads<TX>();
+  constexpr int Q = TX / 4;          // 4-element pieces per tile row
+  constexpr int kRows = NT / Q;      // tile rows loaded per sweep of the CTA
+  constexpr int kOutRows = NT / TX;  // tile rows computed per sweep
   const int x0 = blockIdx.x * TX;
   const size_t off = (size_t)blockIdx.y * so + x0;
   const int ncol = min(TX, nx - x0);
@@ -254,7 +260,7 @@ cudaError_t launch_cols(const char* name, const In* in, uint32_t* out, int L, si
   dim3 grid((nx + TX - 1) / TX, nother);
   {
     TraceScope t(name, s);
-    edt_cols_kernel<TX, In><<<grid, 256, smem, s>>>(in, out, L, sp, nx, so, vec ? 1 : 0);
+    edt_cols_kernel<TX, In><<<grid, cols_threads<TX>(), smem, s>>>(in, out, L, sp, nx, so, vec ? 1 : 0);
   }
   return cudaGetLastError();
 }

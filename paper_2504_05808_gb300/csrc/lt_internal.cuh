@@ -60,7 +60,7 @@ struct ShapeAcc {
 // Defaults: the autotuner's choice for the 512^3 particle volume on GB300.
 struct Tuning {
   int edt_tx_y = 8;             // EDT column-tile width of the y pass for axes <= 512 (32, 16 or 8)
-  int edt_tx_z = 16;            // and of the z pass (its tile rows are a plane apart)
+  int edt_tx_z = 32;            // and of the z pass (32: whole 128-byte tile rows, 512 threads)
   int ridge_z = 32;             // z planes per ridge CTA (8, 16 or 32)
   int paint_blocks_per_sm = 6;  // persistent paint grid, CTAs per SM
 };
