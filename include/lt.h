@@ -120,7 +120,7 @@ lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64
  * Workspace: lt_local_thickness_workspace_size bytes (18 bytes per voxel for
  * the centre list: up to one 16-byte record per voxel, plus part records of
  * big balls that several warps share). The first call on a device also copies lookup tables
- * (about 13 MiB, built once per process on the host) into device memory
+ * (about 26 MiB, built once per process on the host) into device memory
  * owned by the library; make that first call before any stream capture. */
 size_t lt_local_thickness_workspace_size(int ndim, int64_t nx, int64_t ny, int64_t nz);
 lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, int ndim,

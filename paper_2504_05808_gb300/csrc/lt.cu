@@ -44,7 +44,7 @@
 // the label test is skipped.
 //
 // The tables are built once per process on the host and copied once per
-// device into the arrays below (about 23 MiB of device memory).
+// device into the arrays below (about 26 MiB of device memory).
 #include <algorithm>
 #include <climits>
 #include <cstring>
