@@ -16,6 +16,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -70,7 +71,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"lt_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -112,7 +113,8 @@ class ClockSampler:
 
 
 def algorithmic_bytes(name, n, n_surv):
-    """Bytes a kernel must move per launch by its definition."""
+    """Bytes a kernel must move per launch by its definition: the inputs it
+    must read and the outputs it must write, once each."""
     table = {
         "edt_rows_x": 5 * n,          # mask in, g^2 out
         "edt_cols_y": 8 * n,          # u32 in, u32 out

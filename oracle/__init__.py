@@ -27,7 +27,7 @@ and 3D using Local Thickness"):
                        as keeping each object's voxels with LT >= rho).
   roundness_rescaled   R mapped to 0-1 with the reported minimum (Sec. 6.1).
 
-Readings where the paper is garbled or silent (each is listed in the design doc):
+Readings where the paper is garbled or silent:
   * Eqs. 6-7 print e = 1 - c^2/a^2 without a square root; the spheroid's
     eccentricity is e = sqrt(1 - c^2/a^2) (oblate) and sqrt(1 - a^2/c^2)
     (prolate). At c = a both give the sphere, 4 pi a^2.
