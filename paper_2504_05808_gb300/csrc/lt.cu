@@ -1078,7 +1078,7 @@ __device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv,
   const uint32_t nchunks = (n + 31) / 32;
   WorkGrab grab;
   uint32_t ch = 0;
-  while (grab.take(&hdr->ctr_small, nchunks, kChunkGrab, ch)) {
+  while (grab.take(&hdr->ctr_small, nchunks, 1u, ch)) {  // one chunk at a time: 2D chunks vary most in cost
     const uint32_t i = ch * 32 + lane;
     int cnt = 0;
     if (i < n) cnt = make_centre<2>(surv[i], d, sy, sz, touch, dt2, labels, cs[w][lane]);
