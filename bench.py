@@ -29,6 +29,23 @@ METRIC = "Mvoxels/s EDT+LT+shape at 512^3"
 UNIT = "Mvoxels/s"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (x itself with one rank): the job's time
+    is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, voxels_per_rank, seconds):
+    """Mvoxels/s of the whole job: every rank's voxels over the slowest
+    rank's time (weak scaling: each rank measures a volume of its own)."""
+    return world * voxels_per_rank / seconds / 1e6
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -699,11 +716,8 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     trace = lt.lt_trace_summary()
     lt.lt_workspace_status(ws)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nvox / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(world, nvox, ms * 1e-3)
 
     # end to end through the host-buffer entry point (pinned host memory)
     mh = torch.from_numpy(mask).pin_memory()
@@ -719,11 +733,8 @@ def main():
     for _ in range(args.e2e_steps):
         lt.lt_measure_host(mh, lh, n_labels, Sh, Rh, wsh)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * nvox / e2e_s / 1e6, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e = {"value": whole_job_rate(world, nvox, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(mask.nbytes + labels.nbytes),
            "d2h_bytes_per_step": int(2 * 4 * n_labels)}
 
