@@ -148,15 +148,35 @@ def algorithmic_bytes(name, n, n_surv):
 TRAFFIC = {"particles_3d_512": {"edt_rows_x": 344270000, "edt_cols_y": 751800000, "edt_cols_z": 1009210000, "lt_ridge": 1758240000, "lt_paint": 1734620000, "shape_reduce": 848861390}}
 
 
-def update_rate_probe(lt, dev):
+def _probe_lib():
+    """The benchmark's calibration probe (bench_probe.cu, built next to this
+    file by __graft_entry__.build(); not part of the library)."""
+    import ctypes
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_bench_probe.so")
+    lib = ctypes.CDLL(path)
+    lib.probe_update_rate.restype = ctypes.c_int
+    lib.probe_update_rate.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+def update_rate_probe(dev):
     """Atomic-max update ceilings (G updates/s): one line per warp instruction
     or one line per lane, on a 32 MiB (L2-resident) and a 512 MiB buffer."""
+    import ctypes
     import torch
+    lib = _probe_lib()
     out = {}
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     for words, tag in ((1 << 23, "l2"), (1 << 27, "hbm")):
         buf = torch.zeros(words, dtype=torch.int32, device=dev)
         for pat, pname in ((0, "line_per_warp"), (1, "line_per_lane")):
-            out[f"{pname}_{tag}"] = lt.lt_probe_update_rate(buf, pat, reps=5) / 1e9
+            rate = ctypes.c_double(0.0)
+            st = lib.probe_update_rate(ctypes.c_void_p(buf.data_ptr()), words, pat, 5, stream,
+                                       ctypes.byref(rate))
+            if st != 0:
+                raise RuntimeError(f"update-rate probe failed ({st})")
+            out[f"{pname}_{tag}"] = rate.value / 1e9
         del buf
     return out
 
@@ -741,7 +761,7 @@ def main():
     # per-kernel roofline: HBM kernels by algorithmic bytes, painting by
     # updates per second against the probed atomic-update ceiling
     peak, peak_kind = peaks()
-    probe = update_rate_probe(lt, dev) if rank == 0 else None
+    probe = update_rate_probe(dev) if rank == 0 else None
     total_ms = sum(x[1] for x in trace.values())
     kernels = {}
     for k, v in trace.items():
@@ -765,7 +785,7 @@ def main():
         roof = {"kernel": dom, "bound": "atomic", "achieved": kd["achieved_gupd"], "peak": upeak,
                 "unit": "Gupdates/s", "frac": kd["achieved_gupd"] / upeak,
                 "traffic": TRAFFIC.get(args.workload, {}).get(dom), "avg_ms": kd["avg_ms"], "updates": counters["updates"],
-                "peak_source": "measured in this run by lt_probe_update_rate (best of its patterns)",
+                "peak_source": "measured in this run by the atomic-max rate probe (best of its patterns)",
                 "probe_gupd": probe}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": kd.get("achieved_gbs"), "peak": peak,

@@ -1,6 +1,8 @@
-// Calibration probe: the rate of 32-bit atomic-max updates to global memory
-// on this GPU, the ceiling the painting step of local thickness is compared
-// against (painting is nothing but such updates).
+// Calibration probe for the benchmark (not part of the library): the rate of
+// 32-bit atomic-max updates to global memory on this GPU, the ceiling the
+// painting step of local thickness is compared against (painting is nothing
+// but such updates). Built by __graft_entry__.build() into _bench_probe.so,
+// loaded by bench.py only.
 //
 // Pattern 0: the 32 lanes of a warp update the 32 words of one 128-byte line,
 //            so each warp instruction is one line-sized request.
@@ -8,10 +10,15 @@
 //            instruction.
 // Lines are chosen by an integer hash of (warp, iteration[, lane]) over the
 // whole buffer.
-#include "lt_internal.cuh"
+#include <cstddef>
+#include <cstdint>
 
-namespace ltk {
+#include <cuda_runtime.h>
+
 namespace {
+
+// 32-bit integer mixer ("lowbias32" from C. Wellons' hash-prospector, a
+// public-domain xorshift-multiply hash).
 
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
@@ -38,19 +45,25 @@ constexpr uint32_t kProbeIters = 256;
 constexpr int kProbeBlocksPerSm = 8;
 
 }  // namespace
-}  // namespace ltk
 
-using namespace ltk;
-
-extern "C" lt_status lt_probe_update_rate(uint32_t* buf, size_t words, int pattern, int reps, void* stream,
-                                          double* rate) {
-  if (!rate || reps < 1 || (pattern != 0 && pattern != 1)) return LT_ERR_INVALID_ARG;
-  if (words < (1u << 20) || (words & (words - 1)) != 0 || words > (1ull << 36)) return LT_ERR_INVALID_ARG;
-  lt_status st = device_ptr_ok(buf);
-  if (st != LT_OK) return st;
+// Updates per second written to *rate; returns 0 on success, 1 for bad
+// arguments (buf not device memory of the current device, words not a power
+// of two >= 2^20), 2 for a CUDA error. Synchronous.
+extern "C" int probe_update_rate(uint32_t* buf, size_t words, int pattern, int reps, void* stream, double* rate) {
+  if (!rate || !buf || reps < 1 || (pattern != 0 && pattern != 1)) return 1;
+  if (words < (1u << 20) || (words & (words - 1)) != 0 || words > (1ull << 36)) return 1;
+  cudaPointerAttributes a;
+  int cur = -1;
+  if (cudaPointerGetAttributes(&a, buf) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
+      cudaGetDevice(&cur) != cudaSuccess || a.device != cur) {
+    cudaGetLastError();
+    return 1;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur) != cudaSuccess) return 2;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const uint32_t line_mask = (uint32_t)(words / 32 - 1);
-  const unsigned blocks = (unsigned)(sm_count() * kProbeBlocksPerSm);
+  const unsigned blocks = (unsigned)(sms * kProbeBlocksPerSm);
   auto launch = [&]() {
     if (pattern == 0)
       update_probe_kernel<0><<<blocks, 256, 0, s>>>(buf, line_mask, kProbeIters);
@@ -60,7 +73,7 @@ extern "C" lt_status lt_probe_update_rate(uint32_t* buf, size_t words, int patte
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
-    return LT_ERR_CUDA;
+    return 2;
   }
   launch();
   cudaEventRecord(e0, s);
@@ -72,8 +85,8 @@ extern "C" lt_status lt_probe_update_rate(uint32_t* buf, size_t words, int patte
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e != cudaSuccess || ms <= 0.f) return LT_ERR_CUDA;
+  if (e != cudaSuccess || ms <= 0.f) return 2;
   const double updates = (double)blocks * 256.0 * kProbeIters * reps;
   *rate = updates / (ms * 1e-3);
-  return LT_OK;
+  return 0;
 }

@@ -17,6 +17,11 @@
  *               fits in 32 bits. Violations return LT_ERR_DIMS.
  *   Pointers    Device pointers unless the name ends in _host. Device buffers
  *               are owned by the caller and must be 16-byte aligned.
+ *   Device      Every device pointer, the workspace and the stream must
+ *               belong to the calling thread's current device. The library
+ *               never changes the current device; a pointer or stream of
+ *               another device returns LT_ERR_INVALID_ARG before anything is
+ *               enqueued.
  *   Workspace   Scratch memory is always passed in by the caller (`ws`,
  *               `ws_bytes`, 256-byte aligned); the library allocates nothing.
  *               Size it with the matching *_workspace_size function. A
@@ -59,16 +64,18 @@ extern "C" {
 
 typedef enum lt_status {
   LT_OK = 0,
-  LT_ERR_INVALID_ARG = 1,         /* null or misaligned pointer, bad ndim */
+  LT_ERR_INVALID_ARG = 1,         /* null, misaligned or other-device pointer, bad ndim */
   LT_ERR_DIMS = 2,                /* dimensions outside the limits above */
   LT_ERR_WORKSPACE = 3,           /* workspace missing, too small or misaligned */
   LT_ERR_LABEL_RANGE = 4,         /* device-detected: a label >= n_labels */
   LT_ERR_LABEL_OUTSIDE_MASK = 5,  /* device-detected: label != 0 where mask == 0 */
   LT_ERR_CUDA = 6,                /* a CUDA call or kernel launch failed */
   LT_ERR_NO_DEVICE = 7,           /* no usable sm_103 device */
-  LT_ERR_TIMEOUT = 8              /* device-detected: an asynchronous copy did not arrive
+  LT_ERR_TIMEOUT = 8,             /* device-detected: an asynchronous copy did not arrive
                                      within a kernel's wait limit (the kernel stopped early;
                                      outputs are invalid) */
+  LT_ERR_CHECKPOINT = 9           /* checkpoint file unreadable, of another format or
+                                     network shape, or corrupt (CRC mismatch) */
 } lt_status;
 
 /* Per-object sums, one entry per label (structure of arrays, device memory).
@@ -275,6 +282,34 @@ void lt_batch_destroy(lt_batch* batch);
 #define LT_MLP_FEATURES 48
 #define LT_MLP_HIDDEN 64
 #define LT_MLP_PARAMS 7361
+/* Checkpoints of the network and its optimiser (no handle: the network is
+ * the caller's parameter vector, the optimiser state its two moment vectors
+ * and the step count). A checkpoint is lt_mlp_checkpoint_size() bytes,
+ * little-endian: the 8 bytes "LTMLPCK1"; uint32 format version (1),
+ * LT_MLP_FEATURES, LT_MLP_HIDDEN, LT_MLP_PARAMS, the Adam step, flags (bit
+ * 0: moments stored); float32 params, m, v (LT_MLP_PARAMS each, zeros when
+ * no moments are stored); the CRC-32 (IEEE 802.3, as zlib's crc32) of all
+ * bytes before it. Restoring all three vectors and the step and continuing
+ * with the same batches reproduces an uninterrupted run bit for bit.
+ * lt_mlp_checkpoint_pack / _unpack: host buffers only (no GPU needed); m and
+ *   v are given together or both NULL (pack: no moments stored; unpack: not
+ *   read). unpack returns LT_ERR_CHECKPOINT for a wrong size, magic,
+ *   version or network shape, a CRC mismatch, or moments requested from a
+ *   checkpoint that has none; params and step may be NULL.
+ * lt_mlp_save / lt_mlp_load: the same with device vectors (LT_MLP_PARAMS
+ *   floats each) and a file: save copies them to the host on `stream`,
+ *   waits, and writes `path` (through a temporary file renamed into
+ *   place); load reads and checks `path`, then copies to the device on
+ *   `stream` and waits. File errors return LT_ERR_CHECKPOINT. */
+size_t lt_mlp_checkpoint_size(void);
+lt_status lt_mlp_checkpoint_pack(const float* params_host, const float* m_host, const float* v_host,
+                                 uint32_t step, void* out_host, size_t out_bytes);
+lt_status lt_mlp_checkpoint_unpack(const void* in_host, size_t in_bytes, float* params_host, float* m_host,
+                                   float* v_host, uint32_t* step);
+lt_status lt_mlp_save(const char* path, const float* params, const float* m, const float* v, uint32_t step,
+                      void* stream);
+lt_status lt_mlp_load(const char* path, float* params, float* m, float* v, uint32_t* step, void* stream);
+
 size_t lt_features_workspace_size(uint32_t n_labels);
 lt_status lt_object_features(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, int ndim,
                              int64_t nx, int64_t ny, int64_t nz, const lt_object_stats* stats,
@@ -401,20 +436,6 @@ lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, l
  * context stays usable. Workspace: lt_selftest_workspace_size() bytes. */
 size_t lt_selftest_workspace_size(void);
 lt_status lt_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream);
-
-/* ------------------------------------------------------------ calibration --
- * Measures this GPU's rate of 32-bit atomic-max updates to global memory,
- * the operation the painting step consists of, as a ceiling to compare
- * painting against. `buf` (device, `words` uint32, words a power of two
- * >= 2^20, contents overwritten) is the target array: one larger than L2
- * measures updates that go to HBM, a small one updates that stay in L2.
- * pattern 0: each warp updates the 32 words of one 128-byte line per
- *   instruction (the best case: one line per warp instruction);
- * pattern 1: every lane updates a word in a different line (the worst case).
- * Lines are picked by a hash, `reps` timed launches after one warm-up;
- * writes updates per second to *rate. Synchronous (waits for `stream`). */
-lt_status lt_probe_update_rate(uint32_t* buf, size_t words, int pattern, int reps, void* stream,
-                               double* rate);
 
 #ifdef __cplusplus
 }

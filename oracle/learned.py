@@ -209,3 +209,65 @@ def adam_step(params, m, v, grad, step: int, lr: float, beta1=0.9, beta2=0.999, 
     mh = m / (1 - beta1 ** step)
     vh = v / (1 - beta2 ** step)
     return np.asarray(params, np.float64) - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ------------------------------------------------- bound of an FP32 forward
+_U32 = 2.0 ** -24  # unit roundoff of binary32
+_U64 = 2.0 ** -53  # unit roundoff of binary64
+
+
+def _gamma(k: int, u: float) -> float:
+    """Higham's gamma_k = k u / (1 - k u): a sum of k + 1 terms evaluated
+    with k roundings of relative size <= u differs from the exact sum by at
+    most gamma_k times the sum of the terms' magnitudes (any order)."""
+    return k * u / (1.0 - k * u)
+
+
+def _interval_dot(lo: np.ndarray, hi: np.ndarray, W: np.ndarray):
+    """Range of sum_j a_j W[j, k] over a_j in [lo_j, hi_j] (rows of samples),
+    and the largest sum of magnitudes sum_j |a_j W[j, k]|."""
+    Wp, Wn = np.maximum(W, 0.0), np.minimum(W, 0.0)
+    low = lo @ Wp + hi @ Wn
+    high = hi @ Wp + lo @ Wn
+    mag = np.maximum(np.abs(lo), np.abs(hi)) @ np.abs(W)
+    return low, high, mag
+
+
+def mlp_infer_bounds(params: np.ndarray, X: np.ndarray, s_lt: np.ndarray):
+    """Interval [lo, hi] that holds clamp(S_LT + net(x), 0, 1) for any
+    evaluation with this network's rounding points: inputs, weights and both
+    hidden layers rounded to BF16 (nearest even), every dot product plus its
+    bias summed in FP32 in any order (each addition, or fused multiply-add
+    of exact BF16 products, rounded once), S_LT + net rounded to FP32, then
+    clamped. Derived by interval arithmetic: each layer's FP64 sum of the
+    interval ends, widened by gamma_k (FP32) plus gamma_k (FP64) times the
+    sum of magnitudes; bf16(max(t, 0)) is monotone in t, so a layer's
+    activation lies between the roundings of its interval's ends. A sample
+    whose sums all stay clear of a BF16 rounding boundary gets an interval
+    of width ~1e-7; one whose FP32 sum may round either way gets both
+    outcomes. NaN S_LT gives NaN bounds."""
+    W1, b1, W2, b2, w3, b3 = unpack(params)
+    W1q, W2q, w3q = bf16(W1), bf16(W2), bf16(w3)
+    x = bf16(X)
+    # layer 1: exact products of BF16 values, 48 additions onto the bias
+    pre1 = x @ W1q + b1
+    mag1 = np.abs(x) @ np.abs(W1q) + np.abs(b1)
+    e1 = (_gamma(N_FEATURES, _U32) + _gamma(N_FEATURES + 1, _U64)) * mag1
+    h1lo, h1hi = bf16(np.maximum(pre1 - e1, 0.0)), bf16(np.maximum(pre1 + e1, 0.0))
+    # layer 2
+    lo2, hi2, mag2 = _interval_dot(h1lo, h1hi, W2q)
+    e2 = (_gamma(HIDDEN, _U32) + _gamma(HIDDEN + 1, _U64)) * (mag2 + np.abs(b2))
+    h2lo, h2hi = bf16(np.maximum(lo2 + b2 - e2, 0.0)), bf16(np.maximum(hi2 + b2 + e2, 0.0))
+    # output unit
+    lo3, hi3, mag3 = _interval_dot(h2lo, h2hi, w3q.reshape(-1, 1))
+    lo3, hi3, mag3 = lo3[:, 0] + b3, hi3[:, 0] + b3, mag3[:, 0] + abs(b3)
+    e3 = (_gamma(HIDDEN, _U32) + _gamma(HIDDEN + 1, _U64)) * mag3
+    s = np.asarray(s_lt, np.float64)
+    ylo, yhi = s + lo3 - e3, s + hi3 + e3
+    ylo = ylo - (_U32 + _U64) * np.abs(ylo)  # the FP32 rounding of S_LT + net
+    yhi = yhi + (_U32 + _U64) * np.abs(yhi)
+    lo, hi = np.clip(ylo, 0.0, 1.0), np.clip(yhi, 0.0, 1.0)
+    bad = np.isnan(s)
+    lo[bad] = np.nan
+    hi[bad] = np.nan
+    return lo, hi

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lt.so")
 LT_OK = 0
 STATUS_NAMES = {0: "LT_OK", 1: "LT_ERR_INVALID_ARG", 2: "LT_ERR_DIMS", 3: "LT_ERR_WORKSPACE",
                 4: "LT_ERR_LABEL_RANGE", 5: "LT_ERR_LABEL_OUTSIDE_MASK", 6: "LT_ERR_CUDA",
-                7: "LT_ERR_NO_DEVICE", 8: "LT_ERR_TIMEOUT"}
+                7: "LT_ERR_NO_DEVICE", 8: "LT_ERR_TIMEOUT", 9: "LT_ERR_CHECKPOINT"}
 FIXED_POINT_SHIFT = 20
 MLP_FEATURES = 48
 MLP_PARAMS = 7361
@@ -54,7 +54,6 @@ SIGNATURES = {
     "lt_workspace_counters": (_i32, [_vp, _sz, _vp, _vp]),
     "lt_selftest_workspace_size": (_sz, []),
     "lt_selftest_wait_timeout": (_i32, [_vp, _sz, _vp]),
-    "lt_probe_update_rate": (_i32, [_vp, _sz, _i32, _i32, _vp, _vp]),
     "lt_shape_measures_static": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp]),
     "lt_features_workspace_size": (_sz, [_u32]),
     "lt_object_features": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
@@ -64,6 +63,11 @@ SIGNATURES = {
     "lt_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp]),
     "lt_mlp_train_step": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp, _vp, _vp,
                                  _u32, _vp, _sz, _vp, _vp]),
+    "lt_mlp_checkpoint_size": (_sz, []),
+    "lt_mlp_checkpoint_pack": (_i32, [_vp, _vp, _vp, _u32, _vp, _sz]),
+    "lt_mlp_checkpoint_unpack": (_i32, [_vp, _sz, _vp, _vp, _vp, _vp]),
+    "lt_mlp_save": (_i32, [ctypes.c_char_p, _vp, _vp, _vp, _u32, _vp]),
+    "lt_mlp_load": (_i32, [ctypes.c_char_p, _vp, _vp, _vp, _vp, _vp]),
     "lt_batch_workspace_size": (_sz, [_vp, _i32]),
     "lt_batch_create": (_i32, [_vp, _i32, _vp, _sz, _i32, _vp]),
     "lt_batch_run": (_i32, [_vp, _vp]),
@@ -302,20 +306,6 @@ def lt_selftest_wait_timeout(device="cuda", stream=None):
     return lib.lt_selftest_wait_timeout(_ptr(ws), ws.numel(), _stream(stream))
 
 
-def lt_probe_update_rate(buf, pattern, reps=5, stream=None):
-    """Atomic-max updates per second this GPU sustains on `buf` (int32 CUDA
-    tensor, power-of-two length >= 2^20, overwritten); pattern 0: one
-    128-byte line per warp instruction, 1: one line per lane."""
-    import torch
-    if buf.dtype not in (torch.int32, torch.uint32):
-        raise ValueError("expected an int32 tensor")
-    rate = ctypes.c_double()
-    _check(lib.lt_probe_update_rate(_ptr(buf), buf.numel(), pattern, reps, _stream(stream),
-                                    ctypes.byref(rate)), "update-rate probe")
-    return rate.value
-
-
-# ------------------------------------------------------- learned sphericity
 def _stats_struct(stats):
     return ObjectStats(*[stats[k].data_ptr() for k in ("volume", "n_shell", "max_lt2", "sum_lt",
                                                        "sum_shell_lt")])
@@ -368,6 +358,21 @@ def lt_mlp_train_step(params, m, v, grad, step, lr, features, sphericity, target
     return ws
 
 
+def lt_mlp_save(path, params, m=None, v=None, step=0, stream=None):
+    """Writes a checkpoint file of the network (and Adam state) held in
+    device tensors."""
+    _check(lib.lt_mlp_save(os.fsencode(path), _ptr(params), _ptr(m), _ptr(v), int(step), _stream(stream)),
+           "lt_mlp_save")
+
+
+def lt_mlp_load(path, params, m=None, v=None, stream=None):
+    """Reads a checkpoint file into device tensors; returns the Adam step."""
+    step = ctypes.c_uint32(0)
+    _check(lib.lt_mlp_load(os.fsencode(path), _ptr(params), _ptr(m), _ptr(v), ctypes.byref(step),
+                           _stream(stream)), "lt_mlp_load")
+    return int(step.value)
+
+
 def train_mlp(params, features, sphericity, target, train_idx, epochs, batch, lr, order_seed=0):
     """Adam training on the GPU with lt_mlp_train_step. params (FP32 CUDA
     tensor of MLP_PARAMS) is updated in place; train_idx lists the objects
@@ -386,9 +391,10 @@ def train_mlp(params, features, sphericity, target, train_idx, epochs, batch, lr
     step, history = 0, []
     for _ in range(epochs):
         perm = idx[rng.permutation(idx.size)]
+        perm_dev = torch.from_numpy(perm.astype(np.int32)).to(dev)  # one upload per epoch
         losses = []
         for s0 in range(0, perm.size - batch + 1, batch):
-            b = torch.from_numpy(perm[s0:s0 + batch].astype(np.int32)).to(dev)
+            b = perm_dev[s0:s0 + batch]
             step += 1
             lt_mlp_train_step(params, m, v, grad, step, lr, features, sphericity, target, b, loss,
                               ws=ws)

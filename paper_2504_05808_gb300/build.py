@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_lt.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "edt.cu", "lt.cu", "shape.cu", "learned.cu", "batch.cu", "probe.cu", "scaled.cu", "slabs.cu"]
+SOURCES = ["api.cu", "edt.cu", "lt.cu", "shape.cu", "learned.cu", "batch.cu", "scaled.cu", "slabs.cu"]
 
 
 def nvcc() -> str:

@@ -51,9 +51,11 @@ lt_status make_dims(int ndim, int64_t nx, int64_t ny, int64_t nz, Dims* d) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Makes the device that owns `p` current; rejects pointers the GPU cannot
-// address as device memory.
-lt_status use_device_of(const void* p) {
+// Accepts device (or managed) memory of the calling thread's current device
+// only. The library never changes the current device: a pointer that
+// belongs to another device is an argument error, returned before anything
+// is enqueued.
+lt_status on_current_device(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -62,23 +64,35 @@ lt_status use_device_of(const void* p) {
   if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return LT_ERR_INVALID_ARG;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return LT_ERR_CUDA;
-  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return LT_ERR_CUDA;
-  return LT_OK;
+  return a.device == cur ? LT_OK : LT_ERR_INVALID_ARG;
 }
 
 lt_status dev_ptr(const void* p) {
   if (!p || !aligned(p, 16)) return LT_ERR_INVALID_ARG;
-  return use_device_of(p);
+  return on_current_device(p);
 }
 
 lt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LT_OK : LT_ERR_CUDA; }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// The stream must belong to the current device as well (NULL: the legacy
+// default stream, which always does).
+lt_status stream_ok(void* s) {
+  if (!s) return LT_OK;
+  int dev = -1, cur = -1;
+  if (cudaStreamGetDevice(as_stream(s), &dev) != cudaSuccess) {
+    cudaGetLastError();
+    return LT_ERR_INVALID_ARG;
+  }
+  if (cudaGetDevice(&cur) != cudaSuccess) return LT_ERR_CUDA;
+  return dev == cur ? LT_OK : LT_ERR_INVALID_ARG;
+}
+
 lt_status check_ws(void* ws, size_t ws_bytes, size_t need) {
   if (need == 0) return LT_OK;
   if (!ws || !aligned(ws, kAlign) || ws_bytes < need) return LT_ERR_WORKSPACE;
-  return use_device_of(ws);
+  return on_current_device(ws);
 }
 
 size_t measure_body_bytes(const Dims& d, uint32_t n_labels) {
@@ -118,6 +132,7 @@ cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t
 }
 
 lt_status device_ptr_ok(const void* p) { return dev_ptr(p); }
+lt_status stream_on_current_device(void* s) { return stream_ok(s); }
 
 }  // namespace ltk
 
@@ -134,6 +149,7 @@ const char* lt_status_string(lt_status status) {
     case LT_ERR_CUDA: return "CUDA error";
     case LT_ERR_NO_DEVICE: return "no usable CUDA device";
     case LT_ERR_TIMEOUT: return "a kernel's wait for an asynchronous copy reached its limit";
+    case LT_ERR_CHECKPOINT: return "checkpoint unreadable, of another format or network shape, or corrupt";
   }
   return "unknown status";
 }
@@ -151,6 +167,7 @@ lt_status lt_edt(const uint8_t* mask, uint32_t* dt2, int ndim, int64_t nx, int64
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(dt2)) != LT_OK) return st;
   const size_t need = edt_workspace_bytes(d);
   if ((st = check_ws(ws, ws_bytes, need)) != LT_OK) return st;
@@ -169,6 +186,7 @@ lt_status lt_local_thickness(const uint32_t* dt2, const uint32_t* labels, uint32
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if ((st = dev_ptr(dt2)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK)
     return st;
   if ((st = check_ws(ws, ws_bytes, sizeof(WsHeader) + lt_workspace_bytes(d))) != LT_OK) return st;
@@ -193,6 +211,7 @@ lt_status lt_local_thickness_scaled(const uint8_t* mask, const uint32_t* labels,
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (scale < 1 || scale > kMaxScale) return LT_ERR_INVALID_ARG;
   if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK)
     return st;
@@ -223,6 +242,7 @@ lt_status lt_shape_measures_filtered(const uint32_t* labels, const uint32_t* lt2
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (n_labels == 0) return LT_ERR_INVALID_ARG;
   if ((st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(lt2)) != LT_OK) return st;
   if (sphericity && (st = dev_ptr(sphericity)) != LT_OK) return st;
@@ -253,6 +273,7 @@ lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_lab
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (n_labels == 0) return LT_ERR_INVALID_ARG;
   if ((st = dev_ptr(mask)) != LT_OK || (st = dev_ptr(labels)) != LT_OK || (st = dev_ptr(dt2)) != LT_OK ||
       (st = dev_ptr(lt2)) != LT_OK)
@@ -302,6 +323,7 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (n_labels == 0 || !mask_host || !labels_host || !sphericity_host || !roundness_host)
     return LT_ERR_INVALID_ARG;
   size_t off[6];
@@ -382,7 +404,8 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
 
 lt_status lt_workspace_status(const void* ws, size_t ws_bytes, void* stream) {
   if (!ws || ws_bytes < sizeof(WsHeader) || !aligned(ws, kAlign)) return LT_ERR_WORKSPACE;
-  lt_status st = use_device_of(ws);
+  lt_status st = on_current_device(ws);
+  if (st == LT_OK) st = stream_ok(stream);
   if (st != LT_OK) return st;
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
   uint32_t err = 0;
@@ -413,6 +436,7 @@ lt_status lt_measure_slabs(const uint8_t* mask_host, const uint32_t* labels_host
     return LT_ERR_INVALID_ARG;
   if (!slab_dims_ok(nx, ny, nz, slab_planes)) return LT_ERR_DIMS;
   lt_status st = check_ws(ws, ws_bytes, slabs_ws_bytes(n_labels, (int)nx, (int)ny, slab_planes));
+  if (st == LT_OK) st = stream_ok(stream);
   if (st != LT_OK) return st;
   cudaStream_t s = as_stream(stream);
   st = slabs_run(mask_host, labels_host, n_labels, (int)nx, (int)ny, (int)nz, slab_planes, dt2_host, lt2_host,
@@ -432,7 +456,7 @@ lt_status lt_roundness_rescale(const float* roundness, uint32_t n, float r_min, 
   lt_status st;
   if ((st = dev_ptr(roundness)) != LT_OK || (st = dev_ptr(out)) != LT_OK) return st;
   if (!(r_min < 1.f) && !(r_min >= 1.f)) return LT_ERR_INVALID_ARG;  // NaN
-  if ((st = check_ws(ws, ws_bytes, kAlign)) != LT_OK) return st;
+  if ((st = check_ws(ws, ws_bytes, kAlign)) != LT_OK || (st = stream_ok(stream)) != LT_OK) return st;
   return cuda_status(rescale_launch(roundness, n, r_min, reinterpret_cast<uint32_t*>(ws), out, as_stream(stream)));
 }
 
@@ -440,6 +464,7 @@ size_t lt_selftest_workspace_size(void) { return ridge_selftest_bytes(); }
 
 lt_status lt_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream) {
   lt_status st = check_ws(ws, ws_bytes, ridge_selftest_bytes());
+  if (st == LT_OK) st = stream_ok(stream);
   if (st != LT_OK) return st;
   if (ridge_selftest_launch(ws, as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
   return lt_workspace_status(ws, ws_bytes, stream);
@@ -448,7 +473,8 @@ lt_status lt_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream) {
 lt_status lt_workspace_counters(const void* ws, size_t ws_bytes, void* stream, lt_lt_counters* out) {
   if (!ws || ws_bytes < sizeof(WsHeader) || !aligned(ws, kAlign)) return LT_ERR_WORKSPACE;
   if (!out) return LT_ERR_INVALID_ARG;
-  lt_status st = use_device_of(ws);
+  lt_status st = on_current_device(ws);
+  if (st == LT_OK) st = stream_ok(stream);
   if (st != LT_OK) return st;
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return LT_ERR_CUDA;
   WsHeader h;
@@ -586,13 +612,14 @@ lt_status lt_object_features(const uint32_t* labels, const uint32_t* lt2, uint32
   Dims d;
   lt_status st = make_dims(ndim, nx, ny, nz, &d);
   if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (n_labels == 0 || !stats) return LT_ERR_INVALID_ARG;
   const void* ptrs[9] = {labels, lt2, stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt,
                          sphericity, roundness, features};
   for (const void* p : ptrs)
     if ((st = dev_ptr(p)) != LT_OK) return st;
   if (!ws || !aligned(ws, kAlign) || ws_bytes < features_workspace_bytes(n_labels)) return LT_ERR_WORKSPACE;
-  if ((st = use_device_of(ws)) != LT_OK) return st;
+  if ((st = on_current_device(ws)) != LT_OK) return st;
   return cuda_status(features_launch(labels, lt2, n_labels, d, *stats, sphericity, roundness, ws, features,
                                      as_stream(stream)));
 }
@@ -604,6 +631,7 @@ lt_status lt_mlp_infer(const float* params, const float* features, const float* 
   const void* ptrs[4] = {params, features, sphericity, s_learned};
   for (const void* p : ptrs)
     if ((st = dev_ptr(p)) != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   return cuda_status(mlp_infer_launch(params, features, sphericity, n, s_learned, as_stream(stream)));
 }
 
@@ -618,8 +646,9 @@ lt_status lt_mlp_gradients(const float* params, const float* features, const flo
   for (const void* p : ptrs)
     if ((st = dev_ptr(p)) != LT_OK) return st;
   if (loss && (st = dev_ptr(loss)) != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   if (!ws || !aligned(ws, kAlign) || ws_bytes < mlp_train_workspace_bytes(batch)) return LT_ERR_WORKSPACE;
-  if ((st = use_device_of(ws)) != LT_OK) return st;
+  if ((st = on_current_device(ws)) != LT_OK) return st;
   return cuda_status(mlp_grad_launch(params, features, sphericity, target, batch_idx, batch, ws, grad, loss,
                                      as_stream(stream)));
 }
@@ -631,6 +660,7 @@ lt_status lt_mlp_adam(float* params, float* m, float* v, const float* grad, uint
   const void* ptrs[4] = {params, m, v, grad};
   for (const void* p : ptrs)
     if ((st = dev_ptr(p)) != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
   return cuda_status(mlp_adam_launch(params, m, v, grad, step, lr, as_stream(stream)));
 }
 
@@ -642,6 +672,153 @@ lt_status lt_mlp_train_step(float* params, float* m, float* v, float* grad, uint
                                   grad, loss, stream);
   if (st != LT_OK) return st;
   return lt_mlp_adam(params, m, v, grad, step, lr, stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- MLP checkpoints
+// Layout (little-endian): "LTMLPCK1", then uint32 version, n_features,
+// hidden, n_params, step, flags (bit 0: Adam moments stored), then float32
+// params[n_params], m[n_params], v[n_params] (zeros when no moments), then
+// the CRC-32 (IEEE 802.3, reflected, polynomial 0xEDB88320) of every byte
+// before it.
+#include <cstdio>
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'L', 'T', 'M', 'L', 'P', 'C', 'K', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptHeader = 8 + 6 * 4;
+constexpr size_t kCkptBytes = kCkptHeader + 3 * (size_t)LT_MLP_PARAMS * 4 + 4;
+
+// CRC-32 bit by bit from its definition: the remainder of the message
+// polynomial (bits reflected, register preset to all ones, result inverted)
+// modulo x^32 + x^26 + x^23 + ... + 1.
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= p[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return ~c;
+}
+
+void put_u32(unsigned char* p, uint32_t v) {
+  for (int k = 0; k < 4; ++k) p[k] = (unsigned char)(v >> (8 * k));
+}
+uint32_t get_u32(const unsigned char* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+void put_floats(unsigned char* p, const float* v) {
+  for (size_t i = 0; i < (size_t)LT_MLP_PARAMS; ++i) {
+    uint32_t u = 0;
+    if (v) std::memcpy(&u, v + i, 4);
+    put_u32(p + 4 * i, u);
+  }
+}
+void get_floats(const unsigned char* p, float* v) {
+  for (size_t i = 0; i < (size_t)LT_MLP_PARAMS; ++i) {
+    const uint32_t u = get_u32(p + 4 * i);
+    std::memcpy(v + i, &u, 4);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lt_mlp_checkpoint_size(void) { return kCkptBytes; }
+
+lt_status lt_mlp_checkpoint_pack(const float* params_host, const float* m_host, const float* v_host,
+                                 uint32_t step, void* out_host, size_t out_bytes) {
+  if (!params_host || !out_host || (!m_host != !v_host)) return LT_ERR_INVALID_ARG;
+  if (out_bytes < kCkptBytes) return LT_ERR_WORKSPACE;
+  unsigned char* p = reinterpret_cast<unsigned char*>(out_host);
+  std::memcpy(p, kCkptMagic, 8);
+  const uint32_t head[6] = {kCkptVersion, LT_MLP_FEATURES, LT_MLP_HIDDEN, LT_MLP_PARAMS, step,
+                            m_host ? 1u : 0u};
+  for (int k = 0; k < 6; ++k) put_u32(p + 8 + 4 * k, head[k]);
+  unsigned char* body = p + kCkptHeader;
+  put_floats(body, params_host);
+  put_floats(body + 4 * (size_t)LT_MLP_PARAMS, m_host);
+  put_floats(body + 8 * (size_t)LT_MLP_PARAMS, v_host);
+  put_u32(p + kCkptBytes - 4, crc32_ieee(p, kCkptBytes - 4));
+  return LT_OK;
+}
+
+lt_status lt_mlp_checkpoint_unpack(const void* in_host, size_t in_bytes, float* params_host, float* m_host,
+                                   float* v_host, uint32_t* step) {
+  if (!in_host || (!m_host != !v_host)) return LT_ERR_INVALID_ARG;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(in_host);
+  if (in_bytes != kCkptBytes || std::memcmp(p, kCkptMagic, 8) != 0) return LT_ERR_CHECKPOINT;
+  if (get_u32(p + kCkptBytes - 4) != crc32_ieee(p, kCkptBytes - 4)) return LT_ERR_CHECKPOINT;
+  if (get_u32(p + 8) != kCkptVersion || get_u32(p + 12) != LT_MLP_FEATURES || get_u32(p + 16) != LT_MLP_HIDDEN ||
+      get_u32(p + 20) != LT_MLP_PARAMS)
+    return LT_ERR_CHECKPOINT;
+  const bool moments = (get_u32(p + 28) & 1u) != 0;
+  if (m_host && !moments) return LT_ERR_CHECKPOINT;
+  const unsigned char* body = p + kCkptHeader;
+  if (params_host) get_floats(body, params_host);
+  if (m_host) {
+    get_floats(body + 4 * (size_t)LT_MLP_PARAMS, m_host);
+    get_floats(body + 8 * (size_t)LT_MLP_PARAMS, v_host);
+  }
+  if (step) *step = get_u32(p + 24);
+  return LT_OK;
+}
+
+lt_status lt_mlp_save(const char* path, const float* params, const float* m, const float* v, uint32_t step,
+                      void* stream) {
+  if (!path || (!m != !v)) return LT_ERR_INVALID_ARG;
+  lt_status st;
+  const float* ptrs[3] = {params, m, v};
+  for (int k = 0; k < 3; ++k)
+    if ((k == 0 || ptrs[k]) && (st = dev_ptr(ptrs[k])) != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
+  std::vector<float> h(3 * (size_t)LT_MLP_PARAMS);
+  cudaStream_t s = as_stream(stream);
+  for (int k = 0; k < 3; ++k)
+    if (ptrs[k] && cudaMemcpyAsync(h.data() + k * (size_t)LT_MLP_PARAMS, ptrs[k], 4 * (size_t)LT_MLP_PARAMS,
+                                   cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return LT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LT_ERR_CUDA;
+  std::vector<unsigned char> buf(kCkptBytes);
+  st = lt_mlp_checkpoint_pack(h.data(), m ? h.data() + LT_MLP_PARAMS : nullptr,
+                              v ? h.data() + 2 * (size_t)LT_MLP_PARAMS : nullptr, step, buf.data(), buf.size());
+  if (st != LT_OK) return st;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return LT_ERR_CHECKPOINT;
+  const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return LT_ERR_CHECKPOINT;
+  }
+  return LT_OK;
+}
+
+lt_status lt_mlp_load(const char* path, float* params, float* m, float* v, uint32_t* step, void* stream) {
+  if (!path || (!m != !v)) return LT_ERR_INVALID_ARG;
+  lt_status st;
+  float* ptrs[3] = {params, m, v};
+  for (int k = 0; k < 3; ++k)
+    if ((k == 0 || ptrs[k]) && (st = dev_ptr(ptrs[k])) != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
+  std::vector<unsigned char> buf(kCkptBytes + 1);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return LT_ERR_CHECKPOINT;
+  const size_t got = std::fread(buf.data(), 1, buf.size(), f);
+  std::fclose(f);
+  std::vector<float> h(3 * (size_t)LT_MLP_PARAMS);
+  st = lt_mlp_checkpoint_unpack(buf.data(), got, h.data(), m ? h.data() + LT_MLP_PARAMS : nullptr,
+                                v ? h.data() + 2 * (size_t)LT_MLP_PARAMS : nullptr, step);
+  if (st != LT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  for (int k = 0; k < 3; ++k)
+    if (ptrs[k] && cudaMemcpyAsync(ptrs[k], h.data() + k * (size_t)LT_MLP_PARAMS, 4 * (size_t)LT_MLP_PARAMS,
+                                   cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return LT_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? LT_OK : LT_ERR_CUDA;
 }
 
 }  // extern "C"

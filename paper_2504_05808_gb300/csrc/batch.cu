@@ -228,6 +228,15 @@ lt_status time_graph(lt_batch* b, cudaStream_t s, int reps, double* ms) {
   return e == cudaSuccess ? LT_OK : LT_ERR_CUDA;
 }
 
+// A batch runs on the device it was created on, which must be the current
+// device (the library never changes it), with a stream of that device.
+lt_status batch_device_ok(const lt_batch* b, void* stream) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return LT_ERR_CUDA;
+  if (cur != b->device) return LT_ERR_INVALID_ARG;
+  return stream_on_current_device(stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -284,13 +293,14 @@ lt_status lt_batch_create(const lt_volume* vols, int n_vols, void* ws, size_t ws
 
 lt_status lt_batch_run(lt_batch* b, void* stream) {
   if (!b || !b->exec) return LT_ERR_INVALID_ARG;
-  cudaSetDevice(b->device);
+  const lt_status st = batch_device_ok(b, stream);
+  if (st != LT_OK) return st;
   return cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? LT_OK : LT_ERR_CUDA;
 }
 
 lt_status lt_batch_run_eager(lt_batch* b, void* stream) {
   if (!b) return LT_ERR_INVALID_ARG;
-  cudaSetDevice(b->device);
+  if (const lt_status dst = batch_device_ok(b, stream)) return dst;
   for (size_t i = 0; i < b->vols.size(); ++i) {
     const lt_volume& v = b->vols[i];
     if (measure_launch(v.mask, v.labels, v.n_labels, b->dims[i], b->ws + b->off[i], v.dt2, v.lt2,
@@ -302,7 +312,7 @@ lt_status lt_batch_run_eager(lt_batch* b, void* stream) {
 
 lt_status lt_batch_status(lt_batch* b, void* stream) {
   if (!b) return LT_ERR_INVALID_ARG;
-  cudaSetDevice(b->device);
+  if (const lt_status dst = batch_device_ok(b, stream)) return dst;
   lt_status first = LT_OK;
   for (size_t i = 0; i < b->vols.size() && first == LT_OK; ++i) {
     const size_t bytes = measure_ws_bytes(b->dims[i], b->vols[i].n_labels);
@@ -313,7 +323,7 @@ lt_status lt_batch_status(lt_batch* b, void* stream) {
 
 lt_status lt_batch_autotune(lt_batch* b, void* stream, const char* cache_path) {
   if (!b) return LT_ERR_INVALID_ARG;
-  cudaSetDevice(b->device);
+  if (const lt_status dst = batch_device_ok(b, stream)) return dst;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) return LT_ERR_CUDA;
@@ -369,7 +379,6 @@ lt_status lt_batch_settings(const lt_batch* b, int32_t out[5]) {
 
 void lt_batch_destroy(lt_batch* b) {
   if (!b) return;
-  cudaSetDevice(b->device);
   destroy_graph(b);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);

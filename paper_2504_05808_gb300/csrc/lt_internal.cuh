@@ -36,7 +36,7 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 enum : uint32_t { ERR_LABEL_RANGE = 1u, ERR_LABEL_OUTSIDE_MASK = 2u, ERR_TIMEOUT = 4u };
 
 constexpr size_t kAlign = 256;
-inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Floor square root of v < 2^24: IEEE-rounded single-precision square root
 // of an exactly representable integer is within one of the floor; fix it.
@@ -150,7 +150,10 @@ size_t measure_ws_bytes(const Dims& d, uint32_t n_labels);
 cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
                            void* ws, uint32_t* dt2, uint32_t* lt2, float* S, float* R, cudaStream_t s,
                            const Tuning& tu);
+// 16-byte aligned device memory of the current device (the library never
+// changes the current device), and a stream of the current device
 lt_status device_ptr_ok(const void* p);
+lt_status stream_on_current_device(void* s);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

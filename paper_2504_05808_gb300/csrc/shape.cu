@@ -314,7 +314,9 @@ cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* sc
   return cudaGetLastError();
 }
 
-static size_t acc_bytes(uint32_t n) {
+// Accumulator bytes for n labels: three uint32 and two uint64 arrays, each
+// starting on a kAlign boundary (the layout of acc_layout below).
+constexpr size_t acc_bytes(uint32_t n) {
   return 3 * align_up((size_t)n * 4) + 2 * align_up((size_t)n * 8);
 }
 
@@ -408,9 +410,10 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
 
 namespace {
 
-constexpr size_t kStaticScratchBytes =
-    sizeof(ltk::WsHeader) + 3 * ((LT_STATIC_MAX_LABELS * 4 + 255) / 256 * 256) +
-    2 * ((LT_STATIC_MAX_LABELS * 8 + 255) / 256 * 256);
+// Header followed by the accumulators of LT_STATIC_MAX_LABELS labels, the
+// same layout a caller-owned shape workspace has.
+constexpr size_t kStaticScratchBytes = sizeof(ltk::WsHeader) + ltk::acc_bytes(LT_STATIC_MAX_LABELS);
+static_assert(kStaticScratchBytes % ltk::kAlign == 0, "scratch ends on an alignment boundary");
 
 static __device__ __align__(256) unsigned char g_shape_scratch[kStaticScratchBytes];
 
@@ -434,48 +437,30 @@ void* static_scratch() {
   return g_scratch_addr[dev];
 }
 
-bool static_ptr_ok(const void* p) {
-  if (!p || (reinterpret_cast<uintptr_t>(p) % 16) != 0) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return false;
-  return cur == a.device || cudaSetDevice(a.device) == cudaSuccess;
-}
-
 }  // namespace
 
 extern "C" lt_status lt_shape_measures_static(const uint32_t* labels, const uint32_t* lt2,
                                               uint32_t n_labels, int ndim, int64_t nx, int64_t ny,
                                               int64_t nz, float* sphericity, float* roundness,
                                               const lt_object_stats* stats, void* stream) {
-  if (ndim != 2 && ndim != 3) return LT_ERR_INVALID_ARG;
-  if (nx < 1 || ny < 1 || nz < 1 || nx > 8192 || ny > 8192 || nz > 8192) return LT_ERR_DIMS;
-  if (ndim == 2 && nz != 1) return LT_ERR_DIMS;
-  const uint64_t n = (uint64_t)nx * (uint64_t)ny * (uint64_t)nz;
-  if (n >= (1ull << 32)) return LT_ERR_DIMS;
+  ltk::Dims d;
+  lt_status st = ltk::make_dims_checked(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
   if (n_labels == 0) return LT_ERR_INVALID_ARG;
   if (n_labels > LT_STATIC_MAX_LABELS) return LT_ERR_WORKSPACE;
-  if (!static_ptr_ok(labels) || !static_ptr_ok(lt2)) return LT_ERR_INVALID_ARG;
-  if (sphericity && !static_ptr_ok(sphericity)) return LT_ERR_INVALID_ARG;
-  if (roundness && !static_ptr_ok(roundness)) return LT_ERR_INVALID_ARG;
+  static_assert(sizeof(ltk::WsHeader) + ltk::acc_bytes(LT_STATIC_MAX_LABELS) <= kStaticScratchBytes,
+                "the scratch array holds the accumulators of the largest label count");
+  if ((st = ltk::device_ptr_ok(labels)) != LT_OK || (st = ltk::device_ptr_ok(lt2)) != LT_OK) return st;
+  if (sphericity && (st = ltk::device_ptr_ok(sphericity)) != LT_OK) return st;
+  if (roundness && (st = ltk::device_ptr_ok(roundness)) != LT_OK) return st;
   if (stats) {
     const void* arr[5] = {stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt, stats->sum_shell_lt};
     for (const void* p : arr)
-      if (p && !static_ptr_ok(p)) return LT_ERR_INVALID_ARG;
+      if (p && (st = ltk::device_ptr_ok(p)) != LT_OK) return st;
   }
+  if ((st = ltk::stream_on_current_device(stream)) != LT_OK) return st;
   void* scratch = static_scratch();
   if (!scratch) return LT_ERR_CUDA;
-  ltk::Dims d;
-  d.ndim = ndim;
-  d.nx = (int)nx;
-  d.ny = (int)ny;
-  d.nz = (int)nz;
-  d.n = (uint32_t)n;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   ltk::WsHeader* hdr = reinterpret_cast<ltk::WsHeader*>(scratch);
   // the array keeps the previous call's contents: clear the header here; the

@@ -98,6 +98,15 @@ def packed(shape, n_obj, rmin, rmax, seed, f_ell=0.4, f_super=0.3, shrink=(1.0, 
     return mask, labels, int(cnt)
 
 
+def ball(shape, r: int):
+    """One digital ball |x - centre|^2 <= r^2 (integer r, centre at the
+    middle voxel) labelled 1: a solid-dominated volume."""
+    g = np.indices(shape, dtype=np.int64)
+    d2 = sum((g[i] - shape[i] // 2) ** 2 for i in range(len(shape)))
+    mask = (d2 <= r * r).astype(np.uint8)
+    return mask, mask.astype(np.uint32), 1
+
+
 def particles_per_volume(edge: int, ndim: int = 3, voxels_per_particle: float = 512**3 / 5000):
     return max(1, int(round(edge**ndim / voxels_per_particle)))
 
@@ -110,6 +119,12 @@ def workload(name: str, seed: int = 0):
         m, l, c = rsa((128, 128, 128), 50, 4.0, 20.0, seed, bump_frac=0.5)
     elif name == "particles_3d_1024":
         m, l, c = packed((1024, 1024, 1024), 1 << 20, 3.0, 6.0, seed)
+    elif name == "large_3d_256":
+        # big, thick objects (equivalent radius ~20-50, volumes ~1e4-5e5
+        # voxels, the paper's micro-CT range): ellipsoids and superellipsoids
+        m, l, c = packed((256, 256, 256), 40, 20.0, 60.0, seed, f_ell=0.25, f_super=0.75)
+    elif name == "solid_ball_3d_208":
+        m, l, c = ball((208, 208, 208), 100)
     elif name.startswith("particles_3d_"):
         n = int(name.rsplit("_", 1)[1])
         m, l, c = packed((n, n, n), particles_per_volume(n), 8.0, 18.0, seed)

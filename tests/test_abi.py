@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lt):
 
 
 def test_status_strings_and_version(lt):
-    for code in range(9):
+    for code in range(10):
         s = lt.lib.lt_status_string(code)
         assert s and s != b"unknown status"
     assert lt.lib.lt_status_string(99) == b"unknown status"
@@ -113,3 +113,46 @@ def test_batch_argument_errors_need_no_gpu(lt):
     vols[1].nz = 1
     assert L.lt_batch_create(vols, 2, None, 0, 2, ctypes.byref(h)) == E["LT_ERR_INVALID_ARG"]
     assert L.lt_batch_run(None, None) == E["LT_ERR_INVALID_ARG"]
+
+
+def test_mlp_checkpoint_format_needs_no_gpu(lt, tmp_path):
+    """The checkpoint layout through the C ABI on host buffers: the header
+    fields, the float32 vectors in place, the CRC-32 equal to zlib's over the
+    bytes before it, a round trip, and rejection of damaged or foreign data."""
+    import struct
+    import zlib
+    import numpy as np
+    L = lt.lib
+    E = {v: k for k, v in lt.STATUS_NAMES.items()}
+    n = lt.MLP_PARAMS
+    size = L.lt_mlp_checkpoint_size()
+    assert size == 8 + 6 * 4 + 3 * 4 * n + 4
+    rng = np.random.default_rng(0)
+    p, m, v = (rng.normal(size=n).astype(np.float32) for _ in range(3))
+    buf = np.zeros(size, np.uint8)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    assert L.lt_mlp_checkpoint_pack(ptr(p), ptr(m), ptr(v), 1234, ptr(buf), size) == 0
+    raw = buf.tobytes()
+    assert raw[:8] == b"LTMLPCK1"
+    assert struct.unpack("<6I", raw[8:32]) == (1, 48, 64, n, 1234, 1)
+    body = np.frombuffer(raw[32:-4], dtype="<f4")
+    assert np.array_equal(body[:n], p) and np.array_equal(body[n:2 * n], m) and np.array_equal(body[2 * n:], v)
+    assert struct.unpack("<I", raw[-4:])[0] == zlib.crc32(raw[:-4])
+    out = [np.zeros(n, np.float32) for _ in range(3)]
+    step = ctypes.c_uint32(0)
+    assert L.lt_mlp_checkpoint_unpack(ptr(buf), size, *[ptr(a) for a in out], ctypes.byref(step)) == 0
+    assert step.value == 1234 and all(np.array_equal(a, b) for a, b in zip(out, (p, m, v)))
+    for k in (0, 20, 40, size - 1):  # magic, network shape, a weight, the CRC itself
+        bad = buf.copy()
+        bad[k] ^= 1
+        assert L.lt_mlp_checkpoint_unpack(ptr(bad), size, ptr(out[0]), None, None, None) == E["LT_ERR_CHECKPOINT"]
+    assert L.lt_mlp_checkpoint_unpack(ptr(buf), size - 1, ptr(out[0]), None, None, None) == E["LT_ERR_CHECKPOINT"]
+    # without moments: stored as zeros, flag clear, and not readable as moments
+    assert L.lt_mlp_checkpoint_pack(ptr(p), None, None, 7, ptr(buf), size) == 0
+    assert struct.unpack("<I", buf.tobytes()[28:32])[0] == 0
+    assert L.lt_mlp_checkpoint_unpack(ptr(buf), size, ptr(out[0]), ptr(out[1]), ptr(out[2]), None) == \
+        E["LT_ERR_CHECKPOINT"]
+    assert L.lt_mlp_checkpoint_unpack(ptr(buf), size, ptr(out[0]), None, None, None) == 0
+    assert L.lt_mlp_checkpoint_pack(ptr(p), ptr(m), None, 7, ptr(buf), size) == E["LT_ERR_INVALID_ARG"]
+    assert L.lt_mlp_checkpoint_pack(ptr(p), None, None, 7, ptr(buf), size - 1) == E["LT_ERR_WORKSPACE"]
+    assert L.lt_mlp_load(str(tmp_path / "missing").encode(), None, None, None, None, None) == E["LT_ERR_INVALID_ARG"]

@@ -102,8 +102,12 @@ def test_inference_and_adam_match_oracle(lt):
     got = out.cpu().numpy()
     assert np.isnan(got[7])
     ok = ~np.isnan(want)
+    # every output inside the interval that BF16 roundings at the network's
+    # rounding points and FP32 sums in any order allow (oracle-derived)
+    lo, hi = L.mlp_infer_bounds(p, F.astype(np.float64), S)
+    assert np.all((got[ok] >= lo[ok]) & (got[ok] <= hi[ok]))
     err = np.abs(got[ok] - want[ok])
-    assert np.quantile(err, 0.99) <= 1e-5 and err.max() <= 2e-2
+    assert np.quantile(err, 0.99) <= 1e-5
     # one Adam step
     rng = np.random.default_rng(3)
     g = rng.normal(size=lt.MLP_PARAMS).astype(np.float32)
@@ -144,3 +148,45 @@ def test_trained_network_beats_plain_formula(lt):
     mae_plain = np.abs(S_all[5] - held_T).mean()
     mae_learned = np.abs(out.cpu().numpy() - held_T).mean()
     assert mae_learned < 0.5 * mae_plain, (mae_learned, mae_plain)
+
+
+def test_checkpoint_resume_matches_continuous_run(lt, tmp_path):
+    """Eight Adam steps in one go against four steps, a checkpoint written
+    and read back into fresh device tensors, and four more steps: the same
+    bits in the parameters and both moments."""
+    import torch
+    F, S, T, p = _random_problem(5, 2000)
+    rng = np.random.default_rng(9)
+    batches = [torch.from_numpy(rng.choice(len(S), 256, replace=False).astype(np.int32)).cuda()
+               for _ in range(8)]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Fd, Sd, Td = d(F), d(S), d(T)
+
+    def run(params, m, v, first, last):
+        grad = torch.empty_like(params)
+        for k in range(first, last):
+            lt.lt_mlp_train_step(params, m, v, grad, k + 1, 1e-3, Fd, Sd, Td, batches[k])
+
+    ref = [d(p.astype(np.float32)), torch.zeros(lt.MLP_PARAMS, device="cuda"),
+           torch.zeros(lt.MLP_PARAMS, device="cuda")]
+    run(*ref, 0, 8)
+    part = [d(p.astype(np.float32)), torch.zeros(lt.MLP_PARAMS, device="cuda"),
+            torch.zeros(lt.MLP_PARAMS, device="cuda")]
+    run(*part, 0, 4)
+    path = str(tmp_path / "net.ckpt")
+    lt.lt_mlp_save(path, *part, step=4)
+    fresh = [torch.full((lt.MLP_PARAMS,), float("nan"), device="cuda") for _ in range(3)]
+    assert lt.lt_mlp_load(path, *fresh) == 4
+    for a, b in zip(fresh, part):
+        assert torch.equal(a, b)
+    run(*fresh, 4, 8)
+    for a, b in zip(fresh, ref):
+        assert torch.equal(a, b)
+    # a damaged file is refused and leaves the tensors alone
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0xFF
+    open(path, "wb").write(bytes(raw))
+    keep = fresh[0].clone()
+    with pytest.raises(lt.LTError) as e:
+        lt.lt_mlp_load(path, *fresh)
+    assert e.value.status == 9 and torch.equal(fresh[0], keep)

@@ -162,30 +162,61 @@ def test_digital_balls(lt):
         assert abs(R[1] - 1.0) <= 1e-6 and S[1] < 1.0
 
 
-def test_full_size_particles_512_sampled(lt):
-    """The 512^3 particle volume in the benchmark's launch configuration
-    (lt_measure on the whole volume). The oracle checks sampled objects one
-    by one (DT2 and LT2 of every voxel of each sampled object, and its S and
-    R); properties that hold at any size are checked on the whole volume."""
+def test_full_size_particles_512_whole_volume(lt):
+    """The 512^3 particle volume (5,000 objects) in the benchmark's launch
+    configuration (lt_measure on the whole volume), against the oracle on
+    the whole volume: DT2 and LT2 of every voxel bit for bit, S and R of
+    every object within 1e-5, plus properties that hold at any size."""
     mask, labels, n = synth.workload("particles_3d_512", 0)
     d, l2, S, R, _ = gpu_pipeline(lt, mask, labels, n)
-    rng = np.random.default_rng(0)
-    vols = np.bincount(labels.reshape(-1), minlength=n)
-    present = np.flatnonzero(vols[1:]) + 1
-    pick = list(rng.choice(present, 60, replace=False)) + list(present[np.argsort(vols[present])[-8:]])
-    ref = oracle.objects_dt2_lt2(mask, labels, pick)
-    for lab, (idx, dd, ll) in ref.items():
-        assert np.array_equal(d.reshape(-1)[idx], dd), f"DT2 of object {lab}"
-        assert np.array_equal(l2.reshape(-1)[idx], ll), f"LT2 of object {lab}"
-        s_ref, r_ref = oracle.object_measures_from_voxels(labels, idx, ll)
-        assert_close(S[lab], s_ref, f"S of object {lab}")
-        assert_close(R[lab], r_ref, f"R of object {lab}")
+    d_ref = oracle.dt2(mask)
+    assert np.array_equal(d, d_ref), "DT2"
+    del d_ref
+    l_ref = oracle.lt2(d, labels)
+    assert np.array_equal(l2, l_ref), "LT2"
+    S_ref, R_ref, _ = oracle.measures(labels, l_ref, n)
+    assert_close(S, S_ref, "sphericity")
+    assert_close(R, R_ref, "roundness")
     on = labels != 0
     assert np.array_equal(d == 0, mask == 0)
     assert np.all(l2[on] >= d[on]) and np.all(l2[~on] == 0)
+    vols = np.bincount(labels.reshape(-1), minlength=n)
     f = ~np.isnan(S)
     assert np.all(S[f] <= 1 + 1e-6) and np.all(R[f] <= 1 + 1e-6) and np.all(R[f] > 0)
     assert np.isnan(S[0]) and np.array_equal(np.isnan(S[1:]), vols[1:] == 0)
+
+
+def test_large_thick_objects_whole_volume(lt):
+    """Forty big ellipsoids and superellipsoids in 256^3 (equivalent radii
+    ~20-50 voxels, volumes up to ~5e5 voxels, 33% foreground): long EDT scans
+    and many kept centres with r^2 > 200, painted row by row. Whole volume
+    against the oracle."""
+    mask, labels, n = synth.workload("large_3d_256", 0)
+    vols = np.bincount(labels.reshape(-1))[1:]
+    assert vols.max() > 1.5e5 and mask.mean() > 0.32
+    d, l2 = check_full(lt, mask, labels, n)
+    assert np.count_nonzero(d > 400) > 10000  # radii above 20 voxels
+
+
+def test_solid_ball_radius_100(lt):
+    """One digital ball of radius 100 (47% of a 208^3 volume): DT2 against
+    scipy's exact EDT of the padded mask; LT2 by the closed form (every
+    voxel of a digital ball lies in the centre's ball, so LT2 is DT2 at the
+    centre everywhere, the least sum of three squares above r^2 = 10^4, i.e.
+    10001); S and R against the oracle's formulas on that LT2 (R = 1)."""
+    import scipy.ndimage as ndi
+    mask, labels, n = synth.workload("solid_ball_3d_208", 0)
+    d, l2, S, R, _ = gpu_pipeline(lt, mask, labels, n)
+    e = ndi.distance_transform_edt(np.pad(mask, 1))[1:-1, 1:-1, 1:-1]
+    assert np.array_equal(d, np.rint(e * e).astype(np.uint32)), "DT2"
+    c = tuple(s // 2 for s in mask.shape)
+    assert d[c] == 10001
+    want = np.where(mask > 0, np.uint32(10001), np.uint32(0))
+    assert np.array_equal(l2, want), "LT2"
+    S_ref, R_ref, _ = oracle.measures(labels, want, n)
+    assert R_ref[1] == 1.0
+    assert_close(S, S_ref, "sphericity")
+    assert_close(R, R_ref, "roundness")
 
 
 def test_device_detected_errors(lt):
@@ -309,3 +340,34 @@ def test_fixed_point_lt_of_every_small_value(lt, shape):
     assert np.array_equal(got, want)
     assert np.array_equal(stats["sum_shell_lt"].cpu().numpy()[1:], want)  # every one-voxel object is shell
     assert np.array_equal(stats["max_lt2"].cpu().numpy()[1:], np.arange(1, n + 1))
+
+
+def test_pointers_of_another_device_are_rejected(lt):
+    """The library never changes the caller's current device: a host
+    pointer, or (with two GPUs) a buffer or stream of another device, is an
+    argument error returned before anything is enqueued, and the current
+    device stays what it was."""
+    import ctypes
+    import torch
+    E = {v: k for k, v in lt.STATUS_NAMES.items()}
+    m = torch.zeros((8, 8, 8), dtype=torch.uint8, device="cuda")
+    dt2 = torch.empty((8, 8, 8), dtype=torch.int32, device="cuda")
+    host = torch.zeros((8, 8, 8), dtype=torch.uint8).pin_memory()
+    ws = lt.workspace(lt.lib.lt_edt_workspace_size(3, 8, 8, 8), "cuda")
+    args = (3, 8, 8, 8, ctypes.c_void_p(ws.data_ptr()), ws.numel(), None)
+    assert lt.lib.lt_edt(ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(dt2.data_ptr()), *args) == \
+        E["LT_ERR_INVALID_ARG"]
+    assert lt.lib.lt_edt(ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(dt2.data_ptr()), *args) == 0
+    if torch.cuda.device_count() < 2:
+        return
+    dev0 = torch.cuda.current_device()
+    other = (dev0 + 1) % torch.cuda.device_count()
+    dt2_other = torch.empty((8, 8, 8), dtype=torch.int32, device=f"cuda:{other}")
+    assert lt.lib.lt_edt(ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(dt2_other.data_ptr()), *args) == \
+        E["LT_ERR_INVALID_ARG"]
+    assert torch.cuda.current_device() == dev0
+    s_other = torch.cuda.Stream(device=other)
+    assert lt.lib.lt_edt(ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(dt2.data_ptr()), 3, 8, 8, 8,
+                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(s_other.cuda_stream)) == \
+        E["LT_ERR_INVALID_ARG"]
+    assert torch.cuda.current_device() == dev0

@@ -147,3 +147,91 @@ def test_bins_agree_with_real_ratio():
     want = np.minimum(15, np.floor(16 * ratio)).astype(np.int64)
     exact_edge = np.isclose(16 * ratio, np.round(16 * ratio), rtol=0, atol=1e-9)
     assert np.array_equal(b[~exact_edge], want[~exact_edge])
+
+
+def _random_net(seed, n):
+    rng = np.random.default_rng(seed)
+    p = synth.mlp_initial_params(seed).astype(np.float32)
+    p[L.OFF_B1:L.OFF_W2] = rng.normal(size=L.HIDDEN).astype(np.float32) * 0.1
+    p[L.OFF_B2:L.OFF_W3] = rng.normal(size=L.HIDDEN).astype(np.float32) * 0.1
+    p[L.OFF_B3] = np.float32(0.05)
+    X = rng.normal(size=(n, L.N_FEATURES)).astype(np.float32)
+    S = rng.random(n).astype(np.float32)
+    return p, X, S
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bf16_forward_matches_torch_reference(seed):
+    """The oracle's BF16 forward against one written with torch's own
+    bfloat16 conversion and torch.nn.functional.linear in FP64: inputs and
+    weights rounded to BF16, each hidden layer's FP64 pre-activation rounded
+    to FP32 (the precision the sums are taken in) and then to BF16 after the
+    ReLU. The rounded activations agree exactly, the output to FP64 order."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    p, X, _ = _random_net(seed, 3000)
+    t = torch.from_numpy(p).double()
+    W1 = t[L.OFF_W1:L.OFF_B1].reshape(L.N_FEATURES, L.HIDDEN)
+    b1, b2, b3 = t[L.OFF_B1:L.OFF_W2], t[L.OFF_B2:L.OFF_W3], t[L.OFF_B3]
+    W2 = t[L.OFF_W2:L.OFF_B2].reshape(L.HIDDEN, L.HIDDEN)
+    w3 = t[L.OFF_W3:L.OFF_B3]
+    q = lambda a: a.float().to(torch.bfloat16).double()
+    x = q(torch.from_numpy(X).double())
+    h1 = q(torch.relu(F.linear(x, q(W1).T, b1)))
+    h2 = q(torch.relu(F.linear(h1, q(W2).T, b2)))
+    out = F.linear(h2, q(w3).reshape(1, -1), b3.reshape(1)).reshape(-1)
+    got, cache = L.mlp_forward(p, X.astype(np.float64))
+    assert np.array_equal(cache[2], h1.numpy())
+    assert np.array_equal(cache[4], h2.numpy())
+    assert np.allclose(got, out.numpy(), rtol=0, atol=1e-12)
+    assert np.count_nonzero(h1.numpy()) > 0.2 * h1.numel()  # the ReLUs are not all off
+
+
+def _fp32_forward(p, X, S, reverse):
+    """The network in plain float32 numpy, one multiply-add at a time in the
+    given order (forward or reversed), rounding as the network specifies."""
+    b = lambda a: L.bf16(a).astype(np.float32)
+    W1, b1, W2, b2, w3, b3 = [np.asarray(a, np.float32) for a in L.unpack(p)]
+    W1q, W2q, w3q = b(W1), b(W2), b(w3)
+    x = b(X)
+
+    def layer(a, W, bias):
+        acc = np.broadcast_to(np.asarray(bias, np.float32), (a.shape[0], W.shape[1])).copy()
+        rng = range(W.shape[0] - 1, -1, -1) if reverse else range(W.shape[0])
+        for i in rng:
+            acc = (acc + a[:, i:i + 1] * W[i]).astype(np.float32)  # exact product, one rounding
+        return acc
+
+    h1 = b(np.maximum(layer(x, W1q, b1), 0))
+    h2 = b(np.maximum(layer(h1, W2q, b2), 0))
+    out = layer(h2, w3q.reshape(-1, 1), np.float32(b3))[:, 0]
+    return np.clip((S.astype(np.float32) + out).astype(np.float32), 0, 1)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_inference_bounds_hold_float32_evaluations(seed):
+    """mlp_infer_bounds against independent FP32 evaluations in two
+    summation orders: both lie inside; so does the FP64 evaluation. The
+    interval's width is the worst-case FP32 summation error (~1e-5 here),
+    plus a BF16 step wherever a hidden unit's sum may round either way."""
+    p, X, S = _random_net(seed, 4000)
+    S[11] = np.nan
+    lo, hi = L.mlp_infer_bounds(p, X.astype(np.float64), S)
+    assert np.isnan(lo[11]) and np.isnan(hi[11])
+    ok = ~np.isnan(S)
+    for rev in (False, True):
+        y = _fp32_forward(p, X, S, rev)
+        assert np.all((y[ok] >= lo[ok]) & (y[ok] <= hi[ok]))
+    out, _ = L.mlp_forward(p, X.astype(np.float64))
+    y64 = np.clip(S.astype(np.float64) + out, 0, 1)
+    assert np.all((y64[ok] >= lo[ok]) & (y64[ok] <= hi[ok]))
+    width = (hi - lo)[ok]
+    assert np.median(width) <= 5e-5 and width.max() <= 0.05
+    # a mistake in the network (an output bias off by 1e-3) leaves the
+    # interval for most samples
+    bad = p.copy()
+    bad[L.OFF_B3] += np.float32(1e-3)
+    yb = _fp32_forward(bad, X, S, False)
+    inside = (yb[ok] >= lo[ok]) & (yb[ok] <= hi[ok])
+    clamped = (yb[ok] == 0) | (yb[ok] == 1)
+    assert np.count_nonzero(~inside & ~clamped) > 0.8 * np.count_nonzero(~clamped)

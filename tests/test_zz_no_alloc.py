@@ -3,25 +3,36 @@
 It serves callers that cannot allocate device memory (code handed device
 buffers by another framework without an allocator of its own, and loops that
 must not call cudaMalloc after start-up). Its scratch is an array that the
-library keeps in device memory, so this test checks, through the C ABI, that
-two calls in a row (the array keeps the previous call's contents) give the
-same sphericity and roundness as lt_shape_measures with a caller workspace,
-and that label counts beyond the array's capacity are refused.
+library keeps in device memory. It runs the same kernels as
+lt_shape_measures (integer sums, the same FP64 formulas), so this test
+demands the same bits, through the C ABI: sphericity, roundness (NaN
+positions included) and the per-object sums, on two calls in a row (the
+array keeps the previous call's contents). Label counts beyond the array's
+capacity are refused.
 
-The file name makes pytest collect it last; it also runs alone in a fresh
-process (the first call on the device performs the one-time set-up).
+The file name makes pytest collect it last. The first call on a device does
+a one-time set-up (it looks up the array's device address);
+test_first_call_in_a_fresh_process runs the comparison in a new Python
+process whose very first library call is the static entry point.
 """
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
-import synth
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-REL_TOL = 1e-5
 MAX_LABELS = 131072  # LT_STATIC_MAX_LABELS in include/lt.h
+STAT_KEYS = ("volume", "n_shell", "max_lt2", "sum_lt", "sum_shell_lt")
 
 
 @pytest.fixture(scope="module")
@@ -37,6 +48,22 @@ def _dims(shape):
     return (2, shape[1], shape[0], 1) if len(shape) == 2 else (3, shape[2], shape[1], shape[0])
 
 
+def _stats(n):
+    import torch
+    st = {k: torch.full((n,), -1, dtype=torch.int32, device="cuda") for k in STAT_KEYS[:3]}
+    st.update({k: torch.full((n,), -1, dtype=torch.int64, device="cuda") for k in STAT_KEYS[3:]})
+    c = (ctypes.c_void_p * 5)(*[st[k].data_ptr() for k in STAT_KEYS])
+    return st, c
+
+
+def _outputs(n):
+    import torch
+    S = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    R = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    st, c = _stats(n)
+    return S, R, st, c
+
+
 def _lt2_on_device(lt, mask, labels):
     import torch
     m = torch.from_numpy(mask).cuda()
@@ -49,37 +76,66 @@ def _lt2_on_device(lt, mask, labels):
     return lab, lt2
 
 
-def _close(got, ref):
-    assert np.array_equal(np.isnan(got), np.isnan(ref))
-    f = ~np.isnan(ref)
-    err = np.abs(got[f].astype(np.float64) - ref[f]) / np.abs(ref[f].astype(np.float64))
-    assert err.size == 0 or err.max() <= REL_TOL
+def _host(S, R, st):
+    return (S.cpu().numpy(), R.cpu().numpy(), {k: v.cpu().numpy() for k, v in st.items()})
 
 
-def test_static_scratch_matches_workspace_entry(lt):
+def _assert_same_bits(got, ref):
+    for a, b in zip(got[:2], ref[:2]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), "S or R bits differ"
+    for k in STAT_KEYS:
+        assert np.array_equal(got[2][k], ref[2][k]), f"stats {k} differ"
+
+
+def compare_static_with_workspace_entry(lt, static_first):
+    """Static entry point vs lt_shape_measures on two workloads, two static
+    calls in a row each. static_first: the very first library call of the
+    process is the static one (the one-time set-up runs inside it)."""
     import torch
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for name, seed in (("ellipsoids_3d_128", 5), ("ellipses_2d_256", 6)):
         mask, labels, n = synth.workload(name, seed)
-        lab, lt2 = _lt2_on_device(lt, mask, labels)
         nd, nx, ny, nz = _dims(mask.shape)
-        S_ref = torch.empty(n, dtype=torch.float32, device="cuda")
-        R_ref = torch.empty_like(S_ref)
+        if static_first:
+            # no other library call may come first, and the bit comparison
+            # holds for any LT2 volume: take one made from the labels
+            fake = np.where(labels != 0, labels % 97 + 1, 0).astype(np.uint32)
+            lab = torch.from_numpy(labels.view(np.int32)).cuda()
+            lt2 = torch.from_numpy(fake.view(np.int32)).cuda()
+        else:
+            lab, lt2 = _lt2_on_device(lt, mask, labels)
+        runs = []
+        for _ in range(2):  # two calls in a row share the library's array
+            S, R, st, c = _outputs(n)
+            s = lt.lib.lt_shape_measures_static(
+                ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(lt2.data_ptr()), n, nd, nx, ny, nz,
+                ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(R.data_ptr()), c, stream)
+            assert s == 0, lt.lib.lt_status_string(s)
+            torch.cuda.synchronize()
+            runs.append(_host(S, R, st))
+        S_ref, R_ref, st_ref, c_ref = _outputs(n)
         ws = lt.workspace(lt.lib.lt_shape_workspace_size(n), "cuda")
-        assert lt.lib.lt_shape_measures(
+        s = lt.lib.lt_shape_measures(
             ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(lt2.data_ptr()), n, nd, nx, ny, nz,
             ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(S_ref.data_ptr()),
-            ctypes.c_void_p(R_ref.data_ptr()), None, stream) == 0
-        for _ in range(2):  # two calls in a row share the library's array
-            S = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
-            R = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
-            st = lt.lib.lt_shape_measures_static(
-                ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(lt2.data_ptr()), n, nd, nx, ny,
-                nz, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(R.data_ptr()), None, stream)
-            assert st == 0, lt.lib.lt_status_string(st)
-            torch.cuda.synchronize()
-            _close(S.cpu().numpy(), S_ref.cpu().numpy())
-            _close(R.cpu().numpy(), R_ref.cpu().numpy())
+            ctypes.c_void_p(R_ref.data_ptr()), c_ref, stream)
+        assert s == 0, lt.lib.lt_status_string(s)
+        torch.cuda.synchronize()
+        ref = _host(S_ref, R_ref, st_ref)
+        assert np.count_nonzero(np.isnan(ref[0])) >= 1  # label 0 at least
+        for got in runs:
+            _assert_same_bits(got, ref)
+
+
+def test_static_scratch_matches_workspace_entry(lt):
+    compare_static_with_workspace_entry(lt, static_first=False)
+
+
+def test_first_call_in_a_fresh_process(lt):
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--child"], capture_output=True,
+                       text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "static-first ok" in r.stdout
 
 
 def test_static_scratch_refuses_too_many_labels(lt):
@@ -91,3 +147,9 @@ def test_static_scratch_refuses_too_many_labels(lt):
                                          ctypes.c_void_p(lt2.data_ptr()), MAX_LABELS + 1, 2, 8, 8,
                                          1, ctypes.c_void_p(S.data_ptr()), None, None, None)
     assert st == 3  # LT_ERR_WORKSPACE
+
+
+if __name__ == "__main__" and "--child" in sys.argv:
+    import paper_2504_05808_gb300 as _lt
+    compare_static_with_workspace_entry(_lt, static_first=True)
+    print("static-first ok")
