@@ -227,27 +227,43 @@ __device__ __forceinline__ uint32_t cres_combo(const uint16_t* base, int cls, ui
 
 // ---------------------------------------------------------- ridge kernel
 // Clears LT2, validates labels against the mask, sets the `touch` flag,
-// applies the containment test and appends kept centres.
+// applies the containment test, appends kept centres and (optionally) takes
+// the largest DT2 of every object (the largest DT2 of an object is that of
+// its highest-ranked voxel, which no neighbour's ball can hold, so the
+// maximum over kept centres is the maximum over the object).
 //
-// A CTA owns a 32 x 8 (x, y) column tile and marches along z through RZ
-// planes. Halo planes of DT2 and labels (x0-4 .. x0+35, y0-1 .. y0+8) sit in
-// a ring of four shared-memory slots: planes z-1, z, z+1 are read while
-// plane z+2 is in flight. With TMA (row pitch a multiple of 16 bytes) one
-// thread issues a tiled bulk copy per plane and array, completing on the
-// slot's mbarrier, so the next plane loads while this one is tested;
-// otherwise all threads load plane z+1 with plain loads. Outside the array
-// the halo holds (0, 0), which never matches an object label. Per plane, the
-// labelled foreground voxels are compacted to the front of the CTA so that
-// the 26-neighbour (8 in 2D) test runs on full warps; every neighbour is
-// evaluated without early exit. Kept centres collect in one shared buffer
-// (front list from its front, back list from its back) and leave with one
-// global atomic per list whenever another plane might not fit (every ~12
-// planes at 512^3: the two list counters are hot, one atomic per flush
-// keeps them from serialising the CTAs). The front of `surv` gets
-// the centres painted in shared chunks: 3D centres with r^2 <= kCresT, a
-// dominant neighbour and a crescent of at most kChunkCres voxels, and every
-// 2D centre. The back gets those a warp paints alone: bigger crescents and
-// the centres painted row by row.
+// A CTA owns a 64 x 8 (x, y) column tile and marches along z through RZ
+// planes; warp w takes row y0 + w, lane j the voxels x0 + j and x0 + 32 + j.
+// Halo planes of DT2 and labels (x0-4 .. x0+67 so that the TMA x coordinate
+// stays 16-byte aligned; y0-1 .. y0+8) sit in a ring of four shared-memory
+// slots. With TMA (row pitch a multiple of 16 bytes) one thread issues a
+// tiled bulk copy per plane and array, completing on the slot's mbarrier;
+// otherwise all threads load planes with plain loads. Outside the array the
+// halo holds (0, 0), which never matches an object label.
+// Three stages, software-pipelined so that one CTA barrier per plane
+// separates them (iteration z runs stage 1 of plane z, stage 2 of plane
+// z - 1 and stage 3 of plane z - 2, on planes z - 2 .. z of the ring; the
+// lists between stages alternate by plane parity):
+//   stage 1  every voxel: clear LT2, check the label against the mask,
+//            compact the labelled foreground voxels;
+//   stage 2  the compacted voxels, full warps: per neighbour class (1, 2 or
+//            3 nonzero offset coordinates) the largest key (r'^2 << 6 | rank
+//            bit << 5 | offset code) over same-label neighbours; r'^2 against
+//            M(class, r^2) decides containment; a face neighbour in the
+//            foreground with another label sets `touch` (every such pair has
+//            a labelled side, so looking from labelled voxels finds them
+//            all); kept voxels are compacted again with their keys (up to
+//            kKeptQ per plane; a voxel beyond that builds its record here);
+//   stage 3  the kept voxels, full warps: dominant and extra neighbours (a
+//            key ranking above the centre) and the record.
+// Kept centres collect in one shared buffer (front list from its front,
+// back list from its back) and leave with one global atomic per list
+// whenever another plane might not fit (the two list counters are hot, one
+// atomic per flush keeps them from serialising the CTAs). The front of
+// `surv` gets the centres painted in shared chunks: 3D centres with r^2 <=
+// kCresT, a dominant neighbour and a crescent of at most kChunkCres voxels,
+// and every 2D centre. The back gets those a warp paints alone: bigger
+// crescents and the centres painted row by row.
 // Records (uint4). Offset codes: (dz+1)*9 + (dy+1)*3 + (dx+1), 31 for none.
 //   Table centres (3D): x = linear index; y = first crescent voxel; z = r^2 |
 //   dominant code << 8 | codes of up to two more higher-ranked same-label
@@ -259,14 +275,17 @@ __device__ __forceinline__ uint32_t cres_combo(const uint16_t* base, int cls, ui
 //   z = the two extra codes; w = part | parts << 8 (row-mode centres go to
 //   the back list directly; a big one as up to kParts records, one per
 //   part, while the extra records stay within n/8).
-constexpr int kTX = 32, kTY = 8;
+constexpr int kTX = 64, kTY = 8;
+constexpr int kTile = kTX * kTY;                   // voxels per tile plane (2 per thread)
 constexpr int kOX = 4;                             // halo column of x0 (keeps TMA x 16-byte aligned)
-constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 40 x 10 words
-constexpr int kSlotPitch = 416;                    // words per slot: 40 x 10 rounded up to 128 bytes
-constexpr int kSlots = 4;
-constexpr int kListBuf = 512;  // kept centres buffered per CTA (a plane adds at most 256)
+constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 72 x 10 words
+constexpr int kSlotPitch = 736;                    // words per slot: 72 x 10 rounded up to 128 bytes
+constexpr int kSlots = 4;                          // planes z-2 .. z in use, z+1 in flight
+constexpr int kListBuf = 896;  // kept centres buffered per CTA (a plane adds at most kTile)
+constexpr int kKeptQ = 128;    // kept voxels per plane handed from stage 2 to stage 3
 constexpr uint32_t kPlaneBytes = kBX * kBY * 4;
 static_assert(kSlotPitch * 4 % 128 == 0 && kSlotPitch >= kBX * kBY, "slot layout");
+static_assert(kListBuf >= kTile && kSlots == 4 && kKeptQ <= 256, "buffer, ring and list sizes");
 
 // Wait: the time limit of each plane wait. extra_tx: bytes each plane's
 // barrier expects beyond its two copies, 0 except in the timeout self-test,
@@ -276,6 +295,105 @@ struct RidgeWait {
   uint32_t extra_tx = 0;
 };
 
+// The record of kept centre at tile position (tx, ty) of plane zc from its
+// three class keys (see the ridge kernel); also decides which list takes
+// it. Row-mode centres are written to the back of `surv` at once (keepA =
+// keepB = false).
+template <int NDIM>
+__device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3], int tx, int ty, int zc, int x0,
+                                             int y0, const Dims& d, const uint32_t* mt, const uint16_t* sbase,
+                                             uint4* __restrict__ surv, WsHeader* __restrict__ hdr, bool& keepA,
+                                             bool& keepB) {
+  // candidates: per class the largest key when it ranks above c (2 r'^2 +
+  // bit > 2 r^2)
+  int brn[3] = {-1, -1, -1};
+  uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
+#pragma unroll
+  for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
+    if ((kmax[k] >> 5) > 2 * r2) {
+      brn[k] = (int)(kmax[k] >> 6);
+      bcode[k] = kmax[k] & 31u;
+    }
+  uint32_t code = kNoDominant, vstart = 0, best = UINT_MAX;
+  int kd = -1;
+  if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
+    // the candidate whose crescent has the fewest voxels; its voxels in the
+    // order with world x innermost (the alternative order when the offset
+    // has no x component)
+    uint2 ce[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(0u, 0u);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t sz = (ce[k].x >> 23) | ((ce[k].y >> 23) << 9);
+      if (brn[k] >= 0 && sz < best) {
+        best = sz;
+        vstart = (bcode[k] % 3 == 1 ? ce[k].y : ce[k].x) & 0x7FFFFFu;
+        code = bcode[k];
+        kd = k;
+      }
+    }
+  } else {
+    // the candidate whose ball comes closest to containing c's
+    int m[3] = {kNoTable, kNoTable, kNoTable};
+    if (r2 <= kMCap) {
+      m[0] = (int)mt[r2];
+      m[1] = (int)mt[(kMCap + 1) + r2];
+      if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
+    }
+    int bestm = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
+      if (brn[k] >= 0 && brn[k] - m[k] > bestm) {
+        bestm = brn[k] - m[k];
+        code = bcode[k];
+      }
+  }
+  const int x = x0 + tx, y = y0 + ty;
+  const uint32_t v = (uint32_t)(((size_t)zc * d.ny + (size_t)y) * d.nx + (size_t)x);
+  // the other classes' candidates: extra balls a crescent voxel may lie in,
+  // with their r^2 (below M(d, r^2) <= 252 for table centres)
+  uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0xFFFFu, ne = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (NDIM == 3 && k != kd && brn[k] >= 0 && ne < 2) {
+      extra = (extra & ~(31u << (5 * ne))) | (bcode[k] << (5 * ne));
+      er = (er & ~(0xFFu << (8 * ne))) | ((uint32_t)min(brn[k], 0xFE) << (8 * ne));
+      ++ne;
+    }
+  const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
+  uint4 rec;
+  if (NDIM == 3 && tab) {
+    // the ball inside the array: R <= x, x + R < nx per axis, R =
+    // floor(sqrt(r^2)); R <= k exactly when r^2 < (k + 1)^2
+    auto fits = [&](int vv, int nv) {
+      return (int64_t)r2 < (int64_t)(vv + 1) * (vv + 1) && (int64_t)r2 < (int64_t)(nv - vv) * (nv - vv);
+    };
+    const uint32_t inside = fits(x, d.nx) && fits(y, d.ny) && fits(zc, d.nz);
+    rec = make_uint4(v, vstart, r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord, er | (best << 16));
+  } else {
+    rec = make_uint4(v, r2 | (code << 25), extra, 0u);
+  }
+  // small crescents are shared out in chunks; a big one takes a warp
+  keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= (uint32_t)kChunkCres);
+  keepB = !keepA;
+  if (keepB && (NDIM == 2 || !tab)) {
+    // painted row by row, written at once (these centres are rare): a big
+    // ball as kParts records, one per warp sharing it (w = part | parts <<
+    // 8), while the extra records fit their budget of n/8
+    keepB = false;
+    const int side = 2 * (int)isqrt24(r2) + 1;
+    const uint32_t steps = (uint32_t)((NDIM == 3 ? side * side : side) + 31) / 32;  // row steps
+    uint32_t parts = min(kParts, max(1u, steps / kStepsPerPart));
+    if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
+    const uint32_t bb = atomicAdd(&hdr->n_big, parts);
+    for (uint32_t q = 0; q < parts; ++q)
+      surv[record_capacity(d.n) - 1 - (bb + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 8));
+  }
+  return rec;
+}
+
 template <int NDIM, int RZ, bool TMA>
 __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ CUtensorMap map_dt2,
                                                        const __grid_constant__ CUtensorMap map_lab,
@@ -283,16 +401,20 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
                                                        const uint32_t* __restrict__ labels,
                                                        uint32_t* __restrict__ lt2, Dims d,
                                                        uint4* __restrict__ surv,
-                                                       WsHeader* __restrict__ hdr, RidgeWait wt, int z_base) {
+                                                       WsHeader* __restrict__ hdr, RidgeWait wt, int z_base,
+                                                       uint32_t* __restrict__ max_dt2, uint32_t n_labels) {
   __shared__ __align__(128) uint32_t sD[kSlots][kSlotPitch];
   __shared__ __align__(128) uint32_t sL[kSlots][kSlotPitch];
   __shared__ uint4 buf[kListBuf];
-  __shared__ uint16_t work[256];
+  __shared__ uint4 keptq[2][kKeptQ];   // stage 2 -> stage 3: (tile position, class keys), by plane parity
+  __shared__ uint16_t work[2][kTile];  // stage 1 -> stage 2, by plane parity
   __shared__ __align__(8) uint64_t bar[kSlots];
-  __shared__ uint32_t cntA, cntB, baseA, baseB, flags, nwork_s, nkept_s;
-  __shared__ uint4 keptq[256];  // pass 2a -> 2b: tile position, per-class best keys
+  __shared__ uint32_t cntA, cntB, baseA, baseB, flags;
+  // list counts by plane mod 3: filled in one iteration, read in the next,
+  // cleared in the one after
+  __shared__ uint32_t nwork_s[3], nkept_s[3];
   __shared__ uint16_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 2];  // copy of g_cres_base
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int z0 = NDIM == 3 ? blockIdx.z * RZ + z_base : 0;
   const int z1 = NDIM == 3 ? min(d.nz, z0 + RZ) : 1;
@@ -325,236 +447,9 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       sL[s][hy * kBX + hx + kOX - 1] = lv;
     }
   };
-  if (NDIM == 3)
-    for (int i = tid; i < 3 * (kCresT + 1); i += 256) sbase[i] = (uint16_t)g_cres_base[i];
-  if (tid == 0) {
-    cntA = cntB = 0;
-    // after a timeout anywhere in this launch, the remaining CTAs stop at once
-    flags = TMA && (*(volatile uint32_t*)&hdr->error & ERR_TIMEOUT) ? 4u : 0u;
-    nwork_s = nkept_s = 0;
-    if (TMA) {
-      for (int s = 0; s < kSlots; ++s) mbar_init(&bar[s], 1);
-      fence_barrier_init();
-    }
-  }
-  __syncthreads();
-  if (flags & 4u) return;
-  if (TMA) {
-    if (tid == 0)
-      for (int p = z0 - 1; p <= min(z1, z0 + kSlots - 2); ++p) issue(p);
-  } else if (NDIM == 3) {
-    load_plane(z0 - 1);
-    load_plane(z0);
-  } else {
-    load_plane(-1);
-    load_plane(0);
-    load_plane(1);
-  }
-  for (int z = z0; z < z1; ++z) {
-    bool ok = true;
-    if (TMA) {
-      if (z == z0)
-        ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1), wt.limit_ns) &&
-             mbar_wait(&bar[slot_of(z)], parity_of(z), wt.limit_ns);
-      ok = ok && mbar_wait(&bar[slot_of(z + 1)], parity_of(z + 1), wt.limit_ns);
-    } else if (NDIM == 3) {
-      load_plane(z + 1);
-    }
-    if (__syncthreads_or(!ok)) {
-      // a copy did not arrive within the wait limit: record it, wait (again
-      // bounded) for the copies this CTA still has in flight, and stop
-      if (tid == 0) {
-        atomicOr(&hdr->error, ERR_TIMEOUT);
-        for (int p = z - 1; p <= min(z1, z + kSlots - 2); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p), wt.limit_ns);
-      }
-      return;
-    }
-    const uint32_t* Dm = sD[slot_of(z - 1)];
-    const uint32_t* D0 = sD[slot_of(z)];
-    const uint32_t* Dp = sD[slot_of(z + 1)];
-    const uint32_t* Lm = sL[slot_of(z - 1)];
-    const uint32_t* L0 = sL[slot_of(z)];
-    const uint32_t* Lp = sL[slot_of(z + 1)];
-    // pass 1, every voxel of the tile: clear LT2, flags, compaction
-    {
-      const int tx = tid & 31, ty = tid >> 5;
-      const int x = x0 + tx, y = y0 + ty;
-      const bool in = x < d.nx && y < d.ny;
-      const int c = (ty + 1) * kBX + (tx + kOX);
-      const uint32_t md = D0[c], ml = L0[c];
-      bool isw = false, touch = false, bad = false;
-      if (in) {
-        lt2[(size_t)z * plane + (size_t)y * d.nx + x] = 0u;
-        bad = md == 0 && ml != 0;
-        if (md != 0) {
-          touch = (D0[c + 1] && L0[c + 1] != ml) || (D0[c + kBX] && L0[c + kBX] != ml);
-          if (NDIM == 3) touch = touch || (Dp[c] && Lp[c] != ml);
-        }
-        isw = md != 0 && ml != 0;
-      }
-      if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
-      if (__any_sync(kFull, touch) && lane == 0) atomicOr(&flags, 2u);
-      const unsigned bal = __ballot_sync(kFull, isw);
-      uint32_t off = 0;
-      if (lane == 0 && bal) off = atomicAdd(&nwork_s, (uint32_t)__popc(bal));
-      off = __shfl_sync(kFull, off, 0);
-      if (isw) work[off + __popc(bal & below)] = (uint16_t)tid;
-    }
-    __syncthreads();
-    const uint32_t nwork = nwork_s;
-    // pass 2a, compacted labelled foreground voxels: containment test; the
-    // kept ones are compacted again (with their per-class best keys) so that
-    // pass 2b, which builds their records, runs on full warps
-    bool kept = false;
-    uint4 kinfo = make_uint4(0u, 0u, 0u, 0u);
-    if ((uint32_t)tid < nwork) {
-      const int t = work[tid];
-      const int tx = t & 31, ty = t >> 5;
-      const int c = (ty + 1) * kBX + (tx + kOX);
-      const uint32_t r2 = D0[c], l = L0[c];
-      int m[3] = {kNoTable, kNoTable, kNoTable};
-      if (r2 <= kMCap) {
-        m[0] = (int)mt[r2];
-        m[1] = (int)mt[(kMCap + 1) + r2];
-        if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
-      }
-      // per class, the largest key (r'^2 << 6 | rank bit << 5 | offset code)
-      // over same-label neighbours: its r'^2 decides containment, and it is
-      // the candidate dominant when it ranks above c (2 r'^2 + bit > 2 r^2)
-      uint32_t kmax[3] = {0u, 0u, 0u};
-#pragma unroll
-      for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
-        const uint32_t* Dz = dz < 0 ? Dm : (dz == 0 ? D0 : Dp);
-        const uint32_t* Lz = dz < 0 ? Lm : (dz == 0 ? L0 : Lp);
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            const int h = c + dy * kBX + dx;
-            const uint32_t nd = Dz[h], nl = Lz[h];
-            const int k = (dx != 0) + (dy != 0) + (dz != 0) - 1;
-            const uint32_t pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-            const uint32_t key = (nd << 6) | (pos << 5) | (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-            kmax[k] = max(kmax[k], nl == l ? key : 0u);
-          }
-        }
-      }
-      bool pruned = false;
-#pragma unroll
-      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k) pruned = pruned || (int)(kmax[k] >> 6) >= m[k];
-      kept = !pruned;
-      kinfo = make_uint4((uint32_t)t, kmax[0], kmax[1], kmax[2]);
-    }
-    {
-      const unsigned bk = __ballot_sync(kFull, kept);
-      uint32_t off = 0;
-      if (lane == 0 && bk) off = atomicAdd(&nkept_s, (uint32_t)__popc(bk));
-      off = __shfl_sync(kFull, off, 0);
-      if (kept) keptq[off + __popc(bk & below)] = kinfo;
-    }
-    __syncthreads();
-    const uint32_t nkept = nkept_s;
-    // pass 2b, kept centres: dominant, extras and the record
-    bool keepA = false, keepB = false;
-    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
-    if ((uint32_t)tid < nkept) {
-      const uint4 kq = keptq[tid];
-      const int t = (int)kq.x;
-      const int tx = t & 31, ty = t >> 5;
-      const int c = (ty + 1) * kBX + (tx + kOX);
-      const uint32_t r2 = D0[c];
-      const uint32_t kmax[3] = {kq.y, kq.z, kq.w};
-      int brn[3] = {-1, -1, -1};
-      uint32_t bcode[3] = {kNoDominant, kNoDominant, kNoDominant};
-#pragma unroll
-      for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
-        if ((kmax[k] >> 5) > 2 * r2) {
-          brn[k] = (int)(kmax[k] >> 6);
-          bcode[k] = kmax[k] & 31u;
-        }
-      {
-        uint32_t code = kNoDominant, vstart = 0, best = UINT_MAX;
-        int kd = -1;
-        if (NDIM == 3 && r2 <= (uint32_t)kCresT) {
-          // the candidate whose crescent has the fewest voxels; its voxels
-          // in the order with world x innermost (the alternative order when
-          // the offset has no x component)
-          uint2 ce[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-            ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(0u, 0u);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const uint32_t sz = (ce[k].x >> 23) | ((ce[k].y >> 23) << 9);
-            if (brn[k] >= 0 && sz < best) {
-              best = sz;
-              vstart = (bcode[k] % 3 == 1 ? ce[k].y : ce[k].x) & 0x7FFFFFu;
-              code = bcode[k];
-              kd = k;
-            }
-          }
-        } else {
-          // the candidate whose ball comes closest to containing c's
-          int m[3] = {kNoTable, kNoTable, kNoTable};
-          if (r2 <= kMCap) {
-            m[0] = (int)mt[r2];
-            m[1] = (int)mt[(kMCap + 1) + r2];
-            if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
-          }
-          int best = INT_MIN;
-#pragma unroll
-          for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k)
-            if (brn[k] >= 0 && brn[k] - m[k] > best) {
-              best = brn[k] - m[k];
-              code = bcode[k];
-            }
-        }
-        const uint32_t v = (uint32_t)((size_t)z * plane + (size_t)(y0 + ty) * d.nx + (x0 + tx));
-        // the other classes' candidates: extra balls a crescent voxel may lie
-        // in, with their r^2 (below M(d, r^2) <= 252 for table centres)
-        uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0xFFFFu, ne = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (NDIM == 3 && k != kd && brn[k] >= 0 && ne < 2) {
-            extra = (extra & ~(31u << (5 * ne))) | (bcode[k] << (5 * ne));
-            er = (er & ~(0xFFu << (8 * ne))) | ((uint32_t)min(brn[k], 0xFE) << (8 * ne));
-            ++ne;
-          }
-        const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
-        if (NDIM == 3 && tab) {
-          // the ball inside the array: R <= x, x + R < nx per axis, R =
-          // floor(sqrt(r^2)); R <= k exactly when r^2 < (k + 1)^2
-          const int x = x0 + tx, y = y0 + ty;
-          auto fits = [&](int v, int nv) {
-            return (int64_t)r2 < (int64_t)(v + 1) * (v + 1) && (int64_t)r2 < (int64_t)(nv - v) * (nv - v);
-          };
-          const uint32_t inside = fits(x, d.nx) && fits(y, d.ny) && fits(z, d.nz);
-          rec = make_uint4(v, vstart, r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord,
-                           er | (best << 16));
-        } else {
-          rec = make_uint4(v, r2 | (code << 25), extra, 0u);
-        }
-        // small crescents are shared out in chunks; a big one takes a warp
-        keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= (uint32_t)kChunkCres);
-        keepB = !keepA;
-        if (keepB && (NDIM == 2 || !tab)) {
-          // painted row by row, written at once (these centres are rare):
-          // a big ball as kParts records, one per warp sharing it (w = part
-          // | parts << 8), while the extra records fit their budget of n/8
-          keepB = false;
-          const int side = 2 * (int)isqrt24(r2) + 1;
-          const uint32_t steps = (uint32_t)((NDIM == 3 ? side * side : side) + 31) / 32;  // row steps
-          uint32_t parts = min(kParts, max(1u, steps / kStepsPerPart));
-          if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
-          const uint32_t base = atomicAdd(&hdr->n_big, parts);
-          for (uint32_t q = 0; q < parts; ++q)
-            surv[record_capacity(d.n) - 1 - (base + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 8));
-        }
-      }
-    }
-    // at most kListBuf records between flushes: list A grows from the front
-    // of buf, list B from its back
+  // appends records to the shared buffer: list A from its front, list B
+  // from its back (all lanes of the warp call it)
+  auto append = [&](bool keepA, bool keepB, const uint4& rec) {
     const unsigned ba = __ballot_sync(kFull, keepA), bb = __ballot_sync(kFull, keepB);
     if (ba) {
       uint32_t wb = 0;
@@ -568,17 +463,188 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       wb = __shfl_sync(kFull, wb, 0);
       if (keepB) buf[kListBuf - 1 - (wb + __popc(bb & below))] = rec;
     }
-    __syncthreads();  // plane z-1 is free again; the buffer may be flushed
-    if (TMA && tid == 0 && z + kSlots - 1 <= z1) {
-      fence_proxy_async();
-      issue(z + kSlots - 1);
+  };
+  if (NDIM == 3)
+    for (int i = tid; i < 3 * (kCresT + 1); i += 256) sbase[i] = (uint16_t)g_cres_base[i];
+  if (tid == 0) {
+    cntA = cntB = 0;
+    // after a timeout anywhere in this launch, the remaining CTAs stop at once
+    flags = TMA && (*(volatile uint32_t*)&hdr->error & ERR_TIMEOUT) ? 4u : 0u;
+    for (int k = 0; k < 3; ++k) nwork_s[k] = nkept_s[k] = 0;
+    if (TMA) {
+      for (int s = 0; s < kSlots; ++s) mbar_init(&bar[s], 1);
+      fence_barrier_init();
     }
-    if (tid == 0) nwork_s = nkept_s = 0;
-    if (cntA + cntB > kListBuf - 256 || z + 1 == z1) {  // uniform: read after the barrier
-      if (tid == 0) {
-        baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
-        baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
+  }
+  __syncthreads();
+  if (flags & 4u) return;
+  if (TMA) {
+    if (tid == 0)
+      for (int p = z0 - 1; p <= min(z1, z0 + 1); ++p) issue(p);
+  } else {
+    load_plane(z0 - 1);
+  }
+  bool touch = false;  // this thread saw two face-adjacent foreground voxels with different labels
+  for (int z = z0; z <= z1 + 1; ++z) {
+    // plane z (and at the start plane z0 - 1) must have arrived
+    bool ok = true;
+    if (z <= z1) {
+      if (TMA) {
+        if (z == z0) ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1), wt.limit_ns);
+        ok = ok && mbar_wait(&bar[slot_of(z)], parity_of(z), wt.limit_ns);
+      } else {
+        load_plane(z);    // (outside the array: zeros)
+        __syncthreads();  // plain loads of other threads
       }
+    }
+    // stage 1, every voxel of plane z: clear LT2, label check, compaction.
+    // (After a timed-out wait the stages read stale shared memory; they only
+    // write LT2 voxels and records of this tile, and the CTA stops below.)
+    if (z < z1) {
+      const int y = y0 + warp;
+      const uint32_t* D0 = sD[slot_of(z)];
+      const uint32_t* L0 = sL[slot_of(z)];
+      uint16_t* wl = work[z & 1];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int tx = lane + 32 * j, x = x0 + tx;
+        const bool in = x < d.nx && y < d.ny;
+        const int c = (warp + 1) * kBX + (tx + kOX);
+        const uint32_t md = D0[c], ml = L0[c];
+        if (in) lt2[(size_t)z * plane + (size_t)y * d.nx + x] = 0u;
+        bad = bad || (in && md == 0 && ml != 0);
+        const bool isw = in && md != 0 && ml != 0;
+        const unsigned bal = __ballot_sync(kFull, isw);
+        uint32_t off = 0;
+        if (lane == 0 && bal) off = atomicAdd(&nwork_s[z % 3], (uint32_t)__popc(bal));
+        off = __shfl_sync(kFull, off, 0);
+        if (isw) wl[off + __popc(bal & below)] = (uint16_t)(warp * kTX + tx);
+      }
+      if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags, 1u);
+    }
+    // stage 2, the labelled voxels of plane zc = z - 1: containment test
+    if (z > z0 && z <= z1) {
+      const int zc = z - 1;
+      const uint32_t nwork = nwork_s[zc % 3];  // complete: filled before the last barrier
+      const uint32_t* Dm = sD[slot_of(zc - 1)];
+      const uint32_t* D0 = sD[slot_of(zc)];
+      const uint32_t* Dp = sD[slot_of(zc + 1)];
+      const uint32_t* Lm = sL[slot_of(zc - 1)];
+      const uint32_t* L0 = sL[slot_of(zc)];
+      const uint32_t* Lp = sL[slot_of(zc + 1)];
+      const uint16_t* wl = work[zc & 1];
+      uint4* kq = keptq[zc & 1];
+      for (uint32_t base = 0; base < nwork; base += 256) {  // uniform
+        const uint32_t i = base + (uint32_t)tid;
+        bool kept = false;
+        uint32_t r2 = 0, l = 0, t = 0;
+        uint32_t kmax[3] = {0u, 0u, 0u};
+        if (i < nwork) {
+          t = wl[i];
+          const int c = (int)(t / kTX + 1) * kBX + (int)(t % kTX) + kOX;
+          r2 = D0[c];
+          l = L0[c];
+          int m[3] = {kNoTable, kNoTable, kNoTable};
+          if (r2 <= kMCap) {
+            m[0] = (int)mt[r2];
+            m[1] = (int)mt[(kMCap + 1) + r2];
+            if (NDIM == 3) m[2] = (int)mt[2 * (kMCap + 1) + r2];
+          }
+#pragma unroll
+          for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
+            const uint32_t* Dz = dz < 0 ? Dm : (dz == 0 ? D0 : Dp);
+            const uint32_t* Lz = dz < 0 ? Lm : (dz == 0 ? L0 : Lp);
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+              for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const int h = c + dy * kBX + dx;
+                const uint32_t nd = Dz[h], nl = Lz[h];
+                const int k = (dx != 0) + (dy != 0) + (dz != 0) - 1;
+                const uint32_t pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+                const uint32_t key = (nd << 6) | (pos << 5) | (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+                kmax[k] = max(kmax[k], nl == l ? key : 0u);
+                if (k == 0) touch = touch || (nd != 0 && nl != l);
+              }
+            }
+          }
+          bool pruned = false;
+#pragma unroll
+          for (int k = 0; k < (NDIM == 3 ? 3 : 2); ++k) pruned = pruned || (int)(kmax[k] >> 6) >= m[k];
+          kept = !pruned;
+        }
+        // largest DT2 per object: one atomic per group of equal labels in the warp
+        if (max_dt2) {
+          const bool has = kept && l < n_labels;
+          const unsigned act = __ballot_sync(kFull, has);
+          if (has) {
+            const unsigned grp = __match_any_sync(act, l);
+            const uint32_t mx = __reduce_max_sync(grp, r2);
+            if (lane == __ffs(grp) - 1) atomicMax(max_dt2 + l, mx);
+          }
+        }
+        // kept voxels to stage 3; those beyond its list build their record now
+        const unsigned bk = __ballot_sync(kFull, kept);
+        uint32_t off = 0;
+        if (lane == 0 && bk) off = atomicAdd(&nkept_s[zc % 3], (uint32_t)__popc(bk));
+        off = __shfl_sync(kFull, off, 0) + __popc(bk & below);
+        const bool late = kept && off >= (uint32_t)kKeptQ;
+        if (kept && !late) kq[off] = make_uint4(t, kmax[0], kmax[1], kmax[2]);
+        if (__any_sync(kFull, late)) {
+          bool keepA = false, keepB = false;
+          uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+          if (late)
+            rec = make_record<NDIM>(r2, kmax, (int)(t % kTX), (int)(t / kTX), zc, x0, y0, d, mt, sbase, surv, hdr,
+                                    keepA, keepB);
+          append(keepA, keepB, rec);
+        }
+      }
+    }
+    // stage 3, the kept voxels of plane zr = z - 2: records
+    if (z > z0 + 1) {
+      const int zr = z - 2;
+      const uint32_t nkept = min(nkept_s[zr % 3], (uint32_t)kKeptQ);
+      const uint32_t* D0 = sD[slot_of(zr)];
+      const uint4* kq = keptq[zr & 1];
+      if ((uint32_t)(255 - tid) < ((nkept + 31u) & ~31u)) {  // the last warps, whole warps
+        const uint32_t i = (uint32_t)(255 - tid);
+        bool keepA = false, keepB = false;
+        uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+        if (i < nkept) {
+          const uint4 q = kq[i];
+          const int tx = (int)(q.x % kTX), ty = (int)(q.x / kTX);
+          const uint32_t r2 = D0[(ty + 1) * kBX + tx + kOX];
+          const uint32_t kmax[3] = {q.y, q.z, q.w};
+          rec = make_record<NDIM>(r2, kmax, tx, ty, zr, x0, y0, d, mt, sbase, surv, hdr, keepA, keepB);
+        }
+        append(keepA, keepB, rec);
+      }
+    }
+    if (tid == 0) {
+      nwork_s[(z + 1) % 3] = 0;  // plane z - 2's count: read in iteration z - 1, refilled in z + 1
+      nkept_s[z % 3] = 0;        // plane z - 3's count: read in iteration z - 1, refilled in z + 1
+    }
+    // the one barrier of the plane; it also agrees on a timed-out wait
+    if (__syncthreads_or(!ok)) {
+      // record the timeout, wait (again bounded) for the copies this CTA
+      // still has in flight, and stop
+      if (tid == 0) {
+        atomicOr(&hdr->error, ERR_TIMEOUT);
+        for (int p = z; p <= min(z1, z + 1); ++p) mbar_wait(&bar[slot_of(p)], parity_of(p), wt.limit_ns);
+      }
+      return;
+    }
+    // plane z - 2 is free again: its slot takes plane z + 2
+    if (TMA && tid == 0 && z + 2 <= z1) {
+      fence_proxy_async();
+      issue(z + 2);
+    }
+    if (cntA + cntB > kListBuf - kTile || z == z1 + 1) {  // uniform: read after the barrier
+      // the two list atomics from two warps, so that their latencies overlap
+      if (tid == 0) baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
+      if (tid == 32) baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
       __syncthreads();
       for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = buf[i];
       for (uint32_t i = tid; i < cntB; i += 256) surv[record_capacity(d.n) - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
@@ -586,10 +652,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
       if (tid == 0) cntA = cntB = 0;
     }
   }
-  if (tid == 0) {
-    if (flags & 1u) atomicOr(&hdr->error, ERR_LABEL_OUTSIDE_MASK);
-    if (flags & 2u) atomicOr(&hdr->touch, 1u);
-  }
+  if (__syncthreads_or(touch) && tid == 0) atomicOr(&hdr->touch, 1u);
+  if (tid == 0 && (flags & 1u)) atomicOr(&hdr->error, ERR_LABEL_OUTSIDE_MASK);
 }
 
 // ---------------------------------------------------------- paint kernel
@@ -1157,11 +1221,14 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
 template <int NDIM, int RZ>
 void launch_ridge(bool tma, dim3 grid, cudaStream_t s, const CUtensorMap& md, const CUtensorMap& ml,
                   const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d, uint4* surv,
-                  WsHeader* hdr, RidgeWait wt = RidgeWait(), int z_base = 0) {
+                  WsHeader* hdr, RidgeWait wt = RidgeWait(), int z_base = 0, uint32_t* max_dt2 = nullptr,
+                  uint32_t n_labels = 0) {
   if (tma)
-    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base);
+    lt_ridge_kernel<NDIM, RZ, true><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base,
+                                                          max_dt2, n_labels);
   else
-    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base);
+    lt_ridge_kernel<NDIM, RZ, false><<<grid, 256, 0, s>>>(md, ml, dt2, labels, lt2, d, surv, hdr, wt, z_base,
+                                                           max_dt2, n_labels);
 }
 
 }  // namespace
@@ -1232,7 +1299,8 @@ cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s) {
 int ridge_chunk(const Tuning& tu) { return tu.ridge_z == 8 || tu.ridge_z == 32 ? tu.ridge_z : 16; }
 
 cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
-                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi) {
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi,
+                            uint32_t* max_dt2, uint32_t n_labels) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
   uint4* surv = reinterpret_cast<uint4*>(body);
@@ -1255,14 +1323,15 @@ cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_
   const int zb = c_lo * rz;
   {
     TraceScope t("lt_ridge", s);
+    const RidgeWait wt;
     if (d.ndim == 2)
-      launch_ridge<2, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr);
+      launch_ridge<2, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, wt, 0, max_dt2, n_labels);
     else if (rz == 8)
-      launch_ridge<3, 8>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
+      launch_ridge<3, 8>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, wt, zb, max_dt2, n_labels);
     else if (rz == 32)
-      launch_ridge<3, 32>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
+      launch_ridge<3, 32>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, wt, zb, max_dt2, n_labels);
     else
-      launch_ridge<3, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, RidgeWait(), zb);
+      launch_ridge<3, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, wt, zb, max_dt2, n_labels);
   }
   return cudaGetLastError();
 }

@@ -80,8 +80,11 @@ cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2
 // (z_lo a multiple of ridge_chunk(tu); its planes and the one on either side
 // must hold final DT2 and labels), then the painting of every kept centre
 int ridge_chunk(const Tuning& tu);
+// max_dt2 (n_labels entries, may be null): raised (atomic max) to the
+// largest DT2 of each object's voxels in the planes processed
 cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
-                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi);
+                            WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu, int z_lo, int z_hi,
+                            uint32_t* max_dt2 = nullptr, uint32_t n_labels = 0);
 cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                             WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu);
 // timeout self-test of the ridge kernel's bounded waits (see lt.h)
