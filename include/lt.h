@@ -357,6 +357,21 @@ lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_lab
                      int64_t nx, int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2,
                      uint32_t* lt2, float* sphericity, float* roundness, void* stream);
 
+/* lt_measure plus the learned correction's features (see lt_object_features
+ * for their definition) in the same shape pass: the ridge pass of local
+ * thickness also takes every object's largest DT2 (which equals its largest
+ * LT2), so the shape pass bins the LT / max-LT histograms next to the sums
+ * instead of a second pass over labels and LT2. Outputs as lt_measure plus
+ * `features` ([n_labels][48] float, device, required) and, when `stats` is
+ * given, the per-object sums. Feed features and sphericity to lt_mlp_infer.
+ * Workspace: lt_measure_features_workspace_size bytes (lt_measure's plus
+ * 132 bytes per label). */
+size_t lt_measure_features_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz);
+lt_status lt_measure_features(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, int ndim, int64_t nx,
+                              int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2, uint32_t* lt2,
+                              float* sphericity, float* roundness, float* features, const lt_object_stats* stats,
+                              void* stream);
+
 /* Slab form of lt_measure for volumes held in host memory whose working set
  * does not fit the device (or a budget on it): the device works on
  * `slab_planes` z planes at a time (workspace ~30 bytes per voxel of a slab,

@@ -46,6 +46,8 @@ SIGNATURES = {
     "lt_roundness_rescale": (_i32, [_vp, _u32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "lt_measure_workspace_size": (_sz, [_u32] + _DIMS),
     "lt_measure": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "lt_measure_features_workspace_size": (_sz, [_u32] + _DIMS),
+    "lt_measure_features": (_i32, [_vp, _vp, _u32] + _DIMS + [_vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lt_measure_slabs_workspace_size": (_sz, [_u32, _i64, _i64, _i64, _i32]),
     "lt_measure_slabs": (_i32, [_vp, _vp, _u32, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "lt_measure_host_workspace_size": (_sz, [_u32] + _DIMS),
@@ -223,6 +225,20 @@ def lt_measure(mask, labels, n_labels, dt2, lt2, sphericity, roundness, ws=None,
     _check(lib.lt_measure(_ptr(mask), _ptr(labels), n_labels, nd, nx, ny, nz, _ptr(ws), ws.numel(),
                           _ptr(dt2), _ptr(lt2), _ptr(sphericity), _ptr(roundness),
                           _stream(stream)), "lt_measure")
+    return ws
+
+
+def lt_measure_features(mask, labels, n_labels, dt2, lt2, sphericity, roundness, features, stats=None, ws=None,
+                        stream=None):
+    """lt_measure plus the learned correction's features ([n_labels, 48]
+    float32) from the same shape pass; stats (dict of five tensors) optional."""
+    nd, nx, ny, nz = _dims(mask)
+    if ws is None:
+        ws = workspace(lib.lt_measure_features_workspace_size(n_labels, nd, nx, ny, nz), mask.device)
+    st = ctypes.byref(_stats_struct(stats)) if stats is not None else None
+    _check(lib.lt_measure_features(_ptr(mask), _ptr(labels), n_labels, nd, nx, ny, nz, _ptr(ws), ws.numel(),
+                                   _ptr(dt2), _ptr(lt2), _ptr(sphericity), _ptr(roundness), _ptr(features), st,
+                                   _stream(stream)), "lt_measure_features")
     return ws
 
 

@@ -131,6 +131,20 @@ cudaError_t measure_launch(const uint8_t* mask, const uint32_t* labels, uint32_t
   return e;
 }
 
+cudaError_t measure_features_launch(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
+                                    void* ws, uint32_t* ref_max, uint32_t* dt2, uint32_t* lt2, float* S, float* R,
+                                    float* F, const lt_object_stats* stats, cudaStream_t s, const Tuning& tu) {
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+  void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ref_max, 0, (size_t)n_labels * 4, s);
+  if (e == cudaSuccess) e = edt_launch(mask, dt2, d, body, s, tu);
+  if (e == cudaSuccess) e = lt_ridge_launch(dt2, labels, lt2, d, hdr, body, s, tu, 0, d.nz, ref_max, n_labels);
+  if (e == cudaSuccess) e = lt_paint_launch(dt2, labels, lt2, d, hdr, body, s, tu);
+  if (e == cudaSuccess) e = shape_features_launch(labels, lt2, n_labels, d, hdr, body, ref_max, S, R, F, stats, s);
+  return e;
+}
+
 lt_status device_ptr_ok(const void* p) { return dev_ptr(p); }
 lt_status stream_on_current_device(void* s) { return stream_ok(s); }
 
@@ -282,6 +296,46 @@ lt_status lt_measure(const uint8_t* mask, const uint32_t* labels, uint32_t n_lab
   if (roundness && (st = dev_ptr(roundness)) != LT_OK) return st;
   if ((st = check_ws(ws, ws_bytes, sizeof(WsHeader) + measure_body_bytes(d, n_labels))) != LT_OK) return st;
   return run_measure(mask, labels, n_labels, d, ws, dt2, lt2, sphericity, roundness, as_stream(stream));
+}
+
+// lt_measure_features: header, the stages' scratch, then the per-object
+// largest DT2 that the ridge pass writes and the shape pass reads.
+static size_t features_body_bytes(const Dims& d, uint32_t n_labels) {
+  const size_t b = measure_body_bytes(d, n_labels), f = shape_features_bytes(n_labels);
+  return align_up(b > f ? b : f);
+}
+
+size_t lt_measure_features_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz) {
+  Dims d;
+  if (n_labels == 0 || make_dims(ndim, nx, ny, nz, &d) != LT_OK) return 0;
+  return sizeof(WsHeader) + features_body_bytes(d, n_labels) + align_up((size_t)n_labels * 4);
+}
+
+lt_status lt_measure_features(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, int ndim, int64_t nx,
+                              int64_t ny, int64_t nz, void* ws, size_t ws_bytes, uint32_t* dt2, uint32_t* lt2,
+                              float* sphericity, float* roundness, float* features, const lt_object_stats* stats,
+                              void* stream) {
+  Dims d;
+  lt_status st = make_dims(ndim, nx, ny, nz, &d);
+  if (st != LT_OK) return st;
+  if ((st = stream_ok(stream)) != LT_OK) return st;
+  if (n_labels == 0) return LT_ERR_INVALID_ARG;
+  const void* ptrs[5] = {mask, labels, dt2, lt2, features};
+  for (const void* p : ptrs)
+    if ((st = dev_ptr(p)) != LT_OK) return st;
+  if (sphericity && (st = dev_ptr(sphericity)) != LT_OK) return st;
+  if (roundness && (st = dev_ptr(roundness)) != LT_OK) return st;
+  if (stats) {
+    const void* arr[5] = {stats->volume, stats->n_shell, stats->max_lt2, stats->sum_lt, stats->sum_shell_lt};
+    for (const void* p : arr)
+      if (p && (st = dev_ptr(p)) != LT_OK) return st;
+  }
+  const size_t need = lt_measure_features_workspace_size(n_labels, ndim, nx, ny, nz);
+  if ((st = check_ws(ws, ws_bytes, need)) != LT_OK) return st;
+  uint32_t* ref_max =
+      reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + sizeof(WsHeader) + features_body_bytes(d, n_labels));
+  return cuda_status(measure_features_launch(mask, labels, n_labels, d, ws, ref_max, dt2, lt2, sphericity,
+                                             roundness, features, stats, as_stream(stream), Tuning()));
 }
 
 static size_t host_layout(const Dims& d, uint32_t n_labels, size_t off[6]) {

@@ -359,30 +359,32 @@ __global__ void mlp_adam_kernel(float* __restrict__ params, float* __restrict__ 
 
 size_t features_workspace_bytes(uint32_t n_labels) { return align_up((size_t)n_labels * 32 * 4); }
 
+cudaError_t features_hist_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                                 const uint32_t* max_lt2, uint32_t* hist, cudaStream_t s) {
+  TraceScope t("features_hist", s);
+  if (d.nx % 4 == 0) {
+    // 64 threads (256 voxels) per row, 4 rows per CTA
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    if (d.ndim == 3)
+      features_hist4_kernel<3><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, max_lt2, hist);
+    else
+      features_hist4_kernel<2><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, max_lt2, hist);
+  } else {
+    dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
+    if (d.ndim == 3)
+      features_hist_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, max_lt2, hist);
+    else
+      features_hist_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, max_lt2, hist);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                             const lt_object_stats& st, const float* S, const float* R, void* body, float* F,
                             cudaStream_t s) {
   uint32_t* hist = reinterpret_cast<uint32_t*>(body);
   cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)n_labels * 32 * 4, s);
-  if (e != cudaSuccess) return e;
-  {
-    TraceScope t("features_hist", s);
-    if (d.nx % 4 == 0) {
-      // 64 threads (256 voxels) per row, 4 rows per CTA
-      dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
-      if (d.ndim == 3)
-        features_hist4_kernel<3><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
-      else
-        features_hist4_kernel<2><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
-    } else {
-      dim3 grid((d.nx + 255) / 256, d.ny, d.nz);
-      if (d.ndim == 3)
-        features_hist_kernel<3><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
-      else
-        features_hist_kernel<2><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, st.max_lt2, hist);
-    }
-  }
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = features_hist_launch(labels, lt2, n_labels, d, st.max_lt2, hist, s);
   if (e != cudaSuccess) return e;
   {
     TraceScope t("features_final", s);

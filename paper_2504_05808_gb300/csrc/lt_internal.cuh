@@ -120,7 +120,23 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
                          const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2 = 0);
 
+// the shape stage with the learned features in the same pass over the
+// volume: per-object histograms of LT / M (M^2 = ref_max[label], the
+// object's largest LT2) next to the sums, then S, R, features [n][48]
+size_t shape_features_bytes(uint32_t n_labels);
+cudaError_t shape_features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                                  WsHeader* hdr, void* body, const uint32_t* ref_max, float* S, float* R, float* F,
+                                  const lt_object_stats* stats, cudaStream_t s);
+// measure_launch plus the features; ref_max: n_labels uint32 scratch that
+// lives through the whole sequence (the ridge pass fills it)
+cudaError_t measure_features_launch(const uint8_t* mask, const uint32_t* labels, uint32_t n_labels, const Dims& d,
+                                    void* ws, uint32_t* ref_max, uint32_t* dt2, uint32_t* lt2, float* S, float* R,
+                                    float* F, const lt_object_stats* stats, cudaStream_t s, const Tuning& tu);
+
 // learned.cu
+// histogram pass of the features (a separate pass over labels and LT2)
+cudaError_t features_hist_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                                 const uint32_t* max_lt2, uint32_t* hist, cudaStream_t s);
 size_t features_workspace_bytes(uint32_t n_labels);
 cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                             const lt_object_stats& st, const float* S, const float* R, void* body, float* F,

@@ -119,12 +119,48 @@ __device__ __forceinline__ uint4 filter4(uint4 L, const uint32_t* __restrict__ l
                     T.w < min_lt2 ? 0u : L.w);
 }
 
-template <int NDIM, bool FILTER>
+// Bin of LT2 t in an object whose largest LT2 is mx (t <= mx): the largest
+// b in 0..15 with b^2 mx <= 256 t, from a float estimate fixed in integers.
+__device__ __forceinline__ uint32_t lt_bin16(uint32_t t, uint32_t mx) {
+  int b = min(15, (int)(16.0f * sqrtf((float)t / (float)max(mx, 1u))));
+  const unsigned long long T = 256ull * t, M = mx;
+  while (b < 15 && (unsigned long long)((b + 1) * (b + 1)) * M <= T) ++b;
+  while (b > 0 && (unsigned long long)(b * b) * M > T) --b;
+  return (uint32_t)b;
+}
+
+// Sums of one warp's 32 per-thread partials that all belong to one label
+// (or to none), by warp reductions: counts, max and the two fixed-point
+// sums (each split into 16-bit halves whose warp sums fit 32 bits: a
+// thread's partial is at most 4 * 2^32).
+__device__ __forceinline__ void warp_uniform_sums(uint32_t& pk, uint32_t& mx, unsigned long long& q,
+                                                  unsigned long long& qs) {
+  pk = __reduce_add_sync(kFull, pk);
+  mx = __reduce_max_sync(kFull, mx);
+  const uint32_t qh = __reduce_add_sync(kFull, (uint32_t)(q >> 16)), ql = __reduce_add_sync(kFull, (uint32_t)q & 0xFFFFu);
+  const uint32_t sh = __reduce_add_sync(kFull, (uint32_t)(qs >> 16)), sl = __reduce_add_sync(kFull, (uint32_t)qs & 0xFFFFu);
+  q = ((unsigned long long)qh << 16) + ql;
+  qs = ((unsigned long long)sh << 16) + sl;
+}
+
+// Vector form for nx % 4 == 0: a thread covers 4 consecutive voxels of a
+// row (16-byte loads of labels, LT2 and the neighbouring rows), adds the
+// voxels of its first nonzero label locally (voxels of another nonzero label
+// in the same 4, which needs touching objects, go straight to the atomics).
+// A warp whose voxels carry one label (the common case) sums its partials
+// by warp reductions; otherwise runs of equal labels across the warp are
+// combined by a segmented scan as above. With HIST, the voxels are also
+// counted into hist[label][32]: bin b (interior) or 16 + b (shell), b the
+// LT/M bin of lt_bin16 with M^2 = ref_max[label] (the object's largest
+// LT2); equal (label, shell, bin) keys of consecutive voxels are counted
+// together, then runs of equal keys across the warp.
+template <int NDIM, bool FILTER, bool HIST>
 __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
                                                             const uint32_t* __restrict__ lt2, Dims d,
                                                             uint32_t n_labels, ShapeAcc acc,
                                                             WsHeader* __restrict__ hdr, uint32_t min_lt2,
-                                                            int z_lo) {
+                                                            int z_lo, const uint32_t* __restrict__ ref_max,
+                                                            uint32_t* __restrict__ hist) {
   const int lane = threadIdx.x & 31;
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z + z_lo;
@@ -137,6 +173,7 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
   if (__ballot_sync(kFull, any) == 0) return;  // uniform per warp
   uint32_t lab = 0, pk = 0, mx = 0;
   unsigned long long q = 0, qs = 0;
+  uint32_t hkey = 0xFFFFFFFFu, hcnt = 0;  // HIST: this thread's first key and its count
   bool bad = false;
   if (any) {
     const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
@@ -167,60 +204,124 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
       Lf = make_uint4(k == 0 ? lf : Lf.x, k == 1 ? lf : Lf.y, k == 2 ? lf : Lf.z, k == 3 ? lf : Lf.w);
     }
     if (FILTER) L = Lf;
+    uint32_t hprev = 0xFFFFFFFFu, hrun = 0, lref = 0, mref = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       uint32_t l = comp(L, k);
-      if (l == 0) continue;
-      if (l >= n_labels) continue;
-      const uint32_t left = k == 0 ? xl : comp(L, k - 1), right = k == 3 ? xr : comp(L, k + 1);
-      bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l;
-      if (NDIM == 3) s = s || comp(Zm, k) != l || comp(Zp, k) != l;
-      const uint32_t t = comp(T, k);
-      const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
-      if (lab == 0) lab = l;
-      if (l == lab) {
-        pk += 1u | (s ? 1u << 16 : 0u);
-        mx = max(mx, t);
-        q += qq;
-        qs += s ? qq : 0ull;
-      } else {  // a second object within the same four voxels
-        atomicAdd(acc.volume + l, 1u);
-        if (s) atomicAdd(acc.n_shell + l, 1u);
-        atomicAdd(acc.sum_lt + l, (unsigned long long)qq);
-        if (s) atomicAdd(acc.sum_shell_lt + l, (unsigned long long)qq);
-        atomicMax(acc.max_lt2 + l, t);
+      uint32_t hk = 0xFFFFFFFFu;
+      if (l != 0 && l < n_labels) {
+        const uint32_t left = k == 0 ? xl : comp(L, k - 1), right = k == 3 ? xr : comp(L, k + 1);
+        bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l;
+        if (NDIM == 3) s = s || comp(Zm, k) != l || comp(Zp, k) != l;
+        const uint32_t t = comp(T, k);
+        const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
+        if (lab == 0) lab = l;
+        if (l == lab) {
+          pk += 1u | (s ? 1u << 16 : 0u);
+          mx = max(mx, t);
+          q += qq;
+          qs += s ? qq : 0ull;
+        } else {  // a second object within the same four voxels
+          atomicAdd(acc.volume + l, 1u);
+          if (s) atomicAdd(acc.n_shell + l, 1u);
+          atomicAdd(acc.sum_lt + l, (unsigned long long)qq);
+          if (s) atomicAdd(acc.sum_shell_lt + l, (unsigned long long)qq);
+          atomicMax(acc.max_lt2 + l, t);
+        }
+        if (HIST) {
+          if (l != lref) {
+            lref = l;
+            mref = ref_max[l];
+          }
+          hk = l * 32u + (s ? 16u : 0u) + lt_bin16(t, mref);
+        }
+      }
+      if (HIST && hk != hprev) {  // close the previous run of keys
+        if (hprev != 0xFFFFFFFFu) {
+          if (hkey == 0xFFFFFFFFu) {
+            hkey = hprev;
+            hcnt = hrun;
+          } else {
+            atomicAdd(hist + hprev, hrun);
+          }
+        }
+        hprev = hk;
+        hrun = 0;
+      }
+      ++hrun;
+    }
+    if (HIST && hprev != 0xFFFFFFFFu) {
+      if (hkey == 0xFFFFFFFFu) {
+        hkey = hprev;
+        hcnt = hrun;
+      } else if (hprev == hkey) {
+        hcnt += hrun;
+      } else {
+        atomicAdd(hist + hprev, hrun);
       }
     }
   }
   if (__any_sync(kFull, bad) && lane == 0) atomicOr(&hdr->error, ERR_LABEL_RANGE);
-  // segmented inclusive scan over runs of equal labels
-  const uint32_t lprev = __shfl_up_sync(kFull, lab, 1);
-  int seg = (lane == 0 || lprev != lab) ? lane : 0;
+  const unsigned has = __ballot_sync(kFull, lab != 0);
+  const uint32_t l0 = has ? __shfl_sync(kFull, lab, __ffs(has) - 1) : 0u;
+  if (__all_sync(kFull, lab == 0 || lab == l0)) {
+    if (has) {
+      warp_uniform_sums(pk, mx, q, qs);
+      if (lane == 0) {
+        atomicAdd(acc.volume + l0, pk & 0xFFFFu);
+        atomicAdd(acc.n_shell + l0, pk >> 16);
+        atomicAdd(acc.sum_lt + l0, q);
+        atomicAdd(acc.sum_shell_lt + l0, qs);
+        atomicMax(acc.max_lt2 + l0, mx);
+      }
+    }
+  } else {
+    // segmented inclusive scan over runs of equal labels
+    const uint32_t lprev = __shfl_up_sync(kFull, lab, 1);
+    int seg = (lane == 0 || lprev != lab) ? lane : 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(kFull, seg, o);
-    if (lane >= o) seg = max(seg, t);
-  }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, seg, o);
+      if (lane >= o) seg = max(seg, t);
+    }
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t a = __shfl_up_sync(kFull, pk, o);
-    const unsigned long long b = __shfl_up_sync(kFull, q, o);
-    const unsigned long long c = __shfl_up_sync(kFull, qs, o);
-    const uint32_t m = __shfl_up_sync(kFull, mx, o);
-    if (lane - o >= seg) {
-      pk += a;
-      q += b;
-      qs += c;
-      mx = max(mx, m);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t a = __shfl_up_sync(kFull, pk, o);
+      const unsigned long long b = __shfl_up_sync(kFull, q, o);
+      const unsigned long long c = __shfl_up_sync(kFull, qs, o);
+      const uint32_t m = __shfl_up_sync(kFull, mx, o);
+      if (lane - o >= seg) {
+        pk += a;
+        q += b;
+        qs += c;
+        mx = max(mx, m);
+      }
+    }
+    const uint32_t lnext = __shfl_down_sync(kFull, lab, 1);
+    if (lab && (lane == 31 || lnext != lab)) {
+      atomicAdd(acc.volume + lab, pk & 0xFFFFu);
+      atomicAdd(acc.n_shell + lab, pk >> 16);
+      atomicAdd(acc.sum_lt + lab, q);
+      atomicAdd(acc.sum_shell_lt + lab, qs);
+      atomicMax(acc.max_lt2 + lab, mx);
     }
   }
-  const uint32_t lnext = __shfl_down_sync(kFull, lab, 1);
-  if (lab && (lane == 31 || lnext != lab)) {
-    atomicAdd(acc.volume + lab, pk & 0xFFFFu);
-    atomicAdd(acc.n_shell + lab, pk >> 16);
-    atomicAdd(acc.sum_lt + lab, q);
-    atomicAdd(acc.sum_shell_lt + lab, qs);
-    atomicMax(acc.max_lt2 + lab, mx);
+  if (HIST) {
+    // segmented inclusive scan of the counts over runs of equal first keys
+    const uint32_t kprev = __shfl_up_sync(kFull, hkey, 1);
+    int seg = (lane == 0 || kprev != hkey) ? lane : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, seg, o);
+      if (lane >= o) seg = max(seg, t);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t a = __shfl_up_sync(kFull, hcnt, o);
+      if (lane - o >= seg) hcnt += a;
+    }
+    const uint32_t knext = __shfl_down_sync(kFull, hkey, 1);
+    if (hkey != 0xFFFFFFFFu && (lane == 31 || knext != hkey)) atomicAdd(hist + hkey, hcnt);
   }
 }
 
@@ -237,7 +338,8 @@ __device__ double spheroid_area(double a, double c) {
 
 template <int NDIM>
 __global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __restrict__ S,
-                                      float* __restrict__ R, lt_object_stats st) {
+                                      float* __restrict__ R, lt_object_stats st,
+                                      const uint32_t* __restrict__ hist, float* __restrict__ F) {
   const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_labels) return;
   const uint32_t V = l ? acc.volume[l] : 0u;
@@ -268,6 +370,28 @@ __global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __
   }
   if (S) S[l] = (float)sph;
   if (R) R[l] = (float)rnd;
+  if (F) {
+    // the learned correction's features of the object (zero for empty
+    // labels): 0 log(V)/10, 1 log(n_shell)/10, 2 log(M)/4, 3 (mean LT)/M,
+    // 4 R, 5 S, 6-21 interior and 22-37 shell fractions per LT/M bin, 38-47 0
+    float* f = F + (size_t)l * LT_MLP_FEATURES;
+    for (int i = 0; i < LT_MLP_FEATURES; ++i) f[i] = 0.0f;
+    if (V > 0) {
+      const double M = sqrt((double)mx);
+      f[0] = (float)(log((double)V) / 10.0);
+      f[1] = (float)(log((double)ns) / 10.0);
+      f[2] = (float)(log(M) / 4.0);
+      f[3] = (float)((double)sl / 1048576.0 / (double)V / M);
+      f[4] = (float)rnd;
+      f[5] = (float)sph;
+      const uint32_t* h = hist + (size_t)l * 32;
+      const double ni = (double)max(1u, V - ns), nsd = (double)max(1u, ns);
+      for (int b = 0; b < 16; ++b) {
+        f[6 + b] = (float)((double)h[b] / ni);
+        f[22 + b] = (float)((double)h[16 + b] / nsd);
+      }
+    }
+  }
 }
 
 // Roundness mapped to 0-1 with the reported minimum (Sec. 6.1). Step 1:
@@ -329,7 +453,8 @@ void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_label
   if (d.nx % 4 == 0) {
     // 64 threads (256 voxels) per row, 4 rows per CTA
     dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, z_hi - z_lo);
-    shape_reduce4_kernel<NDIM, FILTER><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo);
+    shape_reduce4_kernel<NDIM, FILTER, false>
+        <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo, nullptr, nullptr);
   } else {
     dim3 grid((d.nx + 255) / 256, d.ny, z_hi - z_lo);
     shape_reduce_kernel<NDIM, FILTER><<<grid, 256, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo);
@@ -381,9 +506,9 @@ cudaError_t shape_finalize(int ndim, uint32_t n_labels, void* body, float* S, fl
   {
     TraceScope t("shape_finalize", s);
     if (ndim == 3)
-      shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
+      shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, nullptr, nullptr);
     else
-      shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st);
+      shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, nullptr, nullptr);
   }
   return cudaGetLastError();
 }
@@ -395,6 +520,43 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
   if (e == cudaSuccess) e = shape_accumulate(labels, lt2, n_labels, d, hdr, body, 0, d.nz, s, min_lt2);
   if (e == cudaSuccess) e = shape_finalize(d.ndim, n_labels, body, S, R, stats, s);
   return e;
+}
+
+size_t shape_features_bytes(uint32_t n_labels) { return acc_bytes(n_labels) + align_up((size_t)n_labels * 32 * 4); }
+
+cudaError_t shape_features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
+                                  WsHeader* hdr, void* body, const uint32_t* ref_max, float* S, float* R, float* F,
+                                  const lt_object_stats* stats, cudaStream_t s) {
+  const ShapeAcc acc = acc_layout(body, n_labels);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(body) + acc_bytes(n_labels));
+  cudaError_t e = cudaMemsetAsync(body, 0, shape_features_bytes(n_labels), s);
+  if (e != cudaSuccess) return e;
+  if (d.nx % 4 == 0) {
+    TraceScope t("shape_reduce_features", s);
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    if (d.ndim == 3)
+      shape_reduce4_kernel<3, false, true>
+          <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0u, 0, ref_max, hist);
+    else
+      shape_reduce4_kernel<2, false, true>
+          <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0u, 0, ref_max, hist);
+    e = cudaGetLastError();
+  } else {  // rows not a multiple of 4 voxels: the histograms in a pass of their own
+    e = shape_accumulate(labels, lt2, n_labels, d, hdr, body, 0, d.nz, s, 0u);
+    if (e == cudaSuccess) e = features_hist_launch(labels, lt2, n_labels, d, ref_max, hist, s);
+  }
+  if (e != cudaSuccess) return e;
+  lt_object_stats st = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (stats) st = *stats;
+  const unsigned blocks = (n_labels + 255) / 256;
+  {
+    TraceScope t("shape_finalize_features", s);
+    if (d.ndim == 3)
+      shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, hist, F);
+    else
+      shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, hist, F);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace ltk

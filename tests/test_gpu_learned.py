@@ -58,6 +58,55 @@ def test_features_match_oracle(lt, name):
     assert np.abs(F.cpu().numpy() - F_ref).max() <= 1e-5
 
 
+def _fused(lt, mask, labels, n):
+    """lt_measure_features: (S, R, features, stats) as numpy."""
+    import torch
+    m = torch.from_numpy(mask).cuda()
+    lab = torch.from_numpy(labels.view(np.int32)).cuda()
+    dt2 = torch.empty(mask.shape, dtype=torch.int32, device="cuda")
+    lt2 = torch.empty_like(dt2)
+    S = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    R = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    F = torch.full((n, lt.MLP_FEATURES), -1.0, dtype=torch.float32, device="cuda")
+    stats = {k: torch.empty(n, dtype=torch.int32, device="cuda") for k in ("volume", "n_shell", "max_lt2")}
+    stats.update({k: torch.empty(n, dtype=torch.int64, device="cuda") for k in ("sum_lt", "sum_shell_lt")})
+    ws = lt.lt_measure_features(m, lab, n, dt2, lt2, S, R, F, stats)
+    lt.lt_workspace_status(ws)
+    torch.cuda.synchronize()
+    return S.cpu().numpy(), R.cpu().numpy(), F.cpu().numpy(), {k: v.cpu().numpy() for k, v in stats.items()}
+
+
+@pytest.mark.parametrize("case", ["ellipsoids_3d_128", "ellipses_2d_256", "particles_3d_160", "ragged_3d"])
+def test_fused_features_equal_two_pass_features(lt, case):
+    """lt_measure_features bins the histograms inside the shape pass, with
+    the per-object maximum taken by the ridge pass: the same bits as
+    lt_measure (S, R) and as the separate features pass (features, sums),
+    and the oracle's features within 1e-5. ragged_3d has rows of 75 voxels
+    (the pass without 4-voxel vectors)."""
+    import scipy.ndimage as ndi
+    if case == "ragged_3d":
+        rng = np.random.default_rng(5)
+        f = ndi.gaussian_filter(rng.random((40, 37, 75)), 2.0)
+        m = (f > np.quantile(f, 0.55)).astype(np.uint8)
+        lab = ndi.label(m)[0].astype(np.uint32)
+        n = int(lab.max()) + 1
+    elif case == "particles_3d_160":
+        m, lab, n = synth.training_particles(160, 7)
+    else:
+        m, lab, n = synth.workload(case, 4)
+    S, R, F, st = _fused(lt, m, lab, n)
+    S2, R2, F2 = gpu_objects(lt, m, lab, n)
+    assert np.array_equal(S.view(np.uint32), S2.cpu().numpy().view(np.uint32))
+    assert np.array_equal(R.view(np.uint32), R2.cpu().numpy().view(np.uint32))
+    assert np.array_equal(F.view(np.uint32), F2.cpu().numpy().view(np.uint32))
+    _, l_ref, S_ref, R_ref = oracle.pipeline(m, lab, n)
+    F_ref = L.object_features(lab, l_ref, n, S_ref, R_ref)
+    assert np.abs(F - F_ref).max() <= 1e-5
+    ost = oracle.object_stats(lab, l_ref, n)
+    for k in ("volume", "n_shell", "max_lt2"):
+        assert np.array_equal(st[k].astype(np.int64) & 0xFFFFFFFF, ost[k]), k
+
+
 def _random_problem(seed, n=3000):
     rng = np.random.default_rng(seed)
     F = rng.random((n, L.N_FEATURES)).astype(np.float32)
