@@ -249,26 +249,27 @@ def measure_batch(lt, args, dev):
     return out
 
 
-GOLDEN_TARGETS = os.path.join(ROOT, "tests", "golden", "strict_sphericity_training.txt")
+GOLDEN_TARGETS = os.path.join(ROOT, "tests", "golden", "strict_sphericity_bench.txt")
 
 
 def read_golden_targets(path=GOLDEN_TARGETS):
-    """Strict-sphericity targets written by tests/golden/make_strict_targets.py:
-    {seed: (n_labels, crc32 of the labels, targets with NaN where absent)}."""
-    vols, rows = {}, []
+    """{seed: (n_labels, crc32, smoothed targets, binary targets)} from the
+    text file tests/golden/make_strict_targets.py writes (only oracle code
+    computes the targets; this reads numbers)."""
+    out = {}
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
             p = line.split()
+            seed = int(p[1])
             if p[0] == "volume":
-                vols[int(p[1])] = (int(p[2]), int(p[3]))
+                out[seed] = [int(p[2]), int(p[3]), None, None]
             else:
-                rows.append((int(p[0]), int(p[1]), float(p[2])))
-    out = {seed: (n, c, np.full(n, np.nan)) for seed, (n, c) in vols.items()}
-    for seed, l, t in rows:
-        out[seed][2][l] = t
-    return out
+                T = np.full(out[seed][0], np.nan)
+                T[1:] = np.array(p[2:], dtype=np.float64)
+                out[seed][2 if p[0] == "smooth" else 3] = T
+    return {k: tuple(v) for k, v in out.items()}
 
 
 def labels_crc(lab):
@@ -276,81 +277,113 @@ def labels_crc(lab):
     return zlib.crc32(np.ascontiguousarray(lab, np.uint32).tobytes()) & 0xFFFFFFFF
 
 
-def learned_eval(lt, args, dev):
-    """Train the correction on particles of 5 volumes on the GPU, report MAE
-    against strict sphericity on a 6th (held out), and per-object costs. The
-    targets are the FP64 oracle's, read from tests/golden (written there by
-    tests/golden/make_strict_targets.py for these seeded volumes)."""
+LEARNED_TRAIN = 10  # the first volumes of the golden file train; the rest are held out
+
+
+def learned_eval(lt, args, dev, mask, labels, n_labels):
+    """The learned correction at scale: features of every particle of the
+    golden file's volumes (synth.training_particles(320, seed)) from
+    lt_measure_features, one network per strict-sphericity definition
+    trained on the GPU on the first volumes (~20 k particles) and evaluated
+    on the held-out rest (~100 k), MAE against each definition beside the
+    plain S_LT. Per-object cost on the benchmark volume: lt_measure_features
+    minus lt_measure (the histograms binned in the shape pass) plus
+    lt_mlp_infer, against the plain path's own finalize step."""
     import torch
     import synth
     golden = read_golden_targets()
-    feats, S_all, T_all, t_feat, n_obj_feat = [], [], [], 0.0, 0
-    for seed in range(6):
-        m, lab, n = synth.training_particles(160, 100 + seed)
-        gn, gcrc, gT = golden[100 + seed]
+    seeds = sorted(golden)
+    feats, S_all, T_all, vol_of = [], [], {"smooth": [], "binary": []}, []
+    dt2 = lt2 = F = ws = None
+    for i, seed in enumerate(seeds):
+        m, lab, n = synth.training_particles(320, seed)
+        gn, gcrc, Ts, Tb = golden[seed]
         if gn != n or gcrc != labels_crc(lab):
             raise RuntimeError("training volume differs from the one the golden targets were written for")
         mt = torch.from_numpy(m).to(dev)
         labt = torch.from_numpy(lab.view(np.int32)).to(dev)
-        dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
-        lt2 = torch.empty_like(dt2)
+        if dt2 is None or dt2.shape != m.shape:
+            dt2 = torch.empty(m.shape, dtype=torch.int32, device=dev)
+            lt2 = torch.empty_like(dt2)
         S = torch.empty(n, dtype=torch.float32, device=dev)
         R = torch.empty_like(S)
-        stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
-        stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
-        lt.lt_edt(mt, dt2)
-        lt.lt_local_thickness(dt2, labt, lt2)
-        lt.lt_shape_measures(labt, lt2, n, S, R, stats)
         F = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
-        fws = lt.lt_object_features(labt, lt2, n, stats, S, R, F)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        lt.lt_object_features(labt, lt2, n, stats, S, R, F, ws=fws)
-        e1.record()
-        torch.cuda.synchronize()
-        t_feat += e0.elapsed_time(e1)
-        n_obj_feat += n - 1
-        T = gT
+        ws = lt.lt_measure_features(mt, labt, n, dt2, lt2, S, R, F, ws=ws if ws is not None and
+                                    ws.numel() >= lt.lib.lt_measure_features_workspace_size(n, 3, *m.shape[::-1]) else None)
+        lt.lt_workspace_status(ws)
         Sn = S.cpu().numpy()
-        ok = np.isfinite(T) & np.isfinite(Sn)
+        ok = np.isfinite(Sn) & np.isfinite(Ts) & np.isfinite(Tb)
         ok[0] = False
         feats.append(F.cpu().numpy()[ok])
         S_all.append(Sn[ok])
-        T_all.append(T[ok].astype(np.float32))
-    ntr = sum(len(x) for x in S_all[:5])
-    F = torch.from_numpy(np.concatenate(feats)).to(dev)
-    S = torch.from_numpy(np.concatenate(S_all)).to(dev)
-    T = torch.from_numpy(np.concatenate(T_all)).to(dev)
+        T_all["smooth"].append(Ts[ok].astype(np.float32))
+        T_all["binary"].append(Tb[ok].astype(np.float32))
+        vol_of.append(np.full(int(ok.sum()), i))
+    ntr = sum(len(x) for x in S_all[:LEARNED_TRAIN])
+    Fd = torch.from_numpy(np.concatenate(feats)).to(dev)
+    Sd = torch.from_numpy(np.concatenate(S_all)).to(dev)
+    S_held = np.concatenate(S_all[LEARNED_TRAIN:]).astype(np.float64)
+    res = {"volumes": len(seeds), "objects_train": int(ntr), "objects_held_out": int(len(S_held)),
+           "features": "lt_measure_features (histograms binned in the shape pass)"}
+    out = torch.empty(len(S_held), dtype=torch.float32, device=dev)
+    for name, desc in (("smooth", "smoothed-indicator mesh, mesh volume"),
+                       ("binary", "binary-indicator mesh, voxel count")):
+        Td = torch.from_numpy(np.concatenate(T_all[name])).to(dev)
+        p = torch.from_numpy(synth.mlp_initial_params(0)).to(dev)
+        t0 = time.perf_counter()
+        hist = lt.train_mlp(p, Fd, Sd, Td, np.arange(ntr), epochs=60, batch=256, lr=1e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        lt.lt_mlp_infer(p, Fd[ntr:].contiguous(), Sd[ntr:].contiguous(), out)
+        held_T = np.concatenate(T_all[name][LEARNED_TRAIN:]).astype(np.float64)
+        res[name] = {"target": desc, "mae_plain": float(np.abs(S_held - held_T).mean()),
+                     "mae_learned": float(np.abs(out.cpu().numpy().astype(np.float64) - held_T).mean()),
+                     "train_s": train_s, "final_train_loss": hist[-1]}
+    # per-object cost on the benchmark volume
+    m = torch.from_numpy(mask).to(dev)
+    lab = torch.from_numpy(labels.view(np.int32)).to(dev)
+    dt2 = torch.empty(mask.shape, dtype=torch.int32, device=dev)
+    lt2 = torch.empty_like(dt2)
+    S = torch.empty(n_labels, dtype=torch.float32, device=dev)
+    R = torch.empty_like(S)
+    F = torch.empty((n_labels, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
+    sl = torch.empty(n_labels, dtype=torch.float32, device=dev)
+    wsp = lt.lt_measure(m, lab, n_labels, dt2, lt2, S, R)
+    wsf = lt.lt_measure_features(m, lab, n_labels, dt2, lt2, S, R, F)
     p = torch.from_numpy(synth.mlp_initial_params(0)).to(dev)
-    t0 = time.perf_counter()
-    hist = lt.train_mlp(p, F, S, T, np.arange(ntr), epochs=150, batch=256, lr=1e-3)
-    train_s = time.perf_counter() - t0
-    out = torch.empty(len(S) - ntr, dtype=torch.float32, device=dev)
-    Fh, Sh = F[ntr:].contiguous(), S[ntr:].contiguous()
-    lt.lt_mlp_infer(p, Fh, Sh, out)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_plain = timed(lambda: lt.lt_measure(m, lab, n_labels, dt2, lt2, S, R, ws=wsp))
+    t_feat = timed(lambda: lt.lt_measure_features(m, lab, n_labels, dt2, lt2, S, R, F, ws=wsf))
+    t_inf = timed(lambda: lt.lt_mlp_infer(p, F, S, sl))
+    lt.lt_trace_enable(True)
+    for _ in range(10):
+        lt.lt_measure(m, lab, n_labels, dt2, lt2, S, R, ws=wsp)
+        lt.lt_measure_features(m, lab, n_labels, dt2, lt2, S, R, F, ws=wsf)
     torch.cuda.synchronize()
-    held_T = T_all[5].astype(np.float64)
-    res = {"mae_plain": float(np.abs(S_all[5] - held_T).mean()),
-           "mae_learned": float(np.abs(out.cpu().numpy() - held_T).mean()),
-           "objects_train": int(ntr), "objects_held_out": int(len(held_T)),
-           "train_s": train_s, "final_train_loss": hist[-1],
-           "target": "strict sphericity: smoothed marching-tetrahedra mesh (FP64 oracle)",
-           "features_ns_per_object": t_feat * 1e6 / max(1, n_obj_feat)}
-    # inference cost per object at scale (1M objects of random features)
-    big = 1 << 20
-    Fb = torch.rand((big, lt.MLP_FEATURES), device=dev)
-    Sb = torch.rand(big, device=dev)
-    ob = torch.empty(big, device=dev)
-    lt.lt_mlp_infer(p, Fb, Sb, ob)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(5):
-        lt.lt_mlp_infer(p, Fb, Sb, ob)
-    e1.record()
-    torch.cuda.synchronize()
-    res["infer_ns_per_object"] = e0.elapsed_time(e1) / 5 * 1e6 / big
+    lt.lt_trace_enable(False)
+    tr = {k: v[1] / max(1, v[0]) for k, v in lt.lt_trace_summary().items()}
+    objs = n_labels - 1
+    res["cost_512"] = {
+        "objects": objs, "plain_ms": t_plain, "with_features_ms": t_feat, "infer_ms": t_inf,
+        "features_ns_per_object": (t_feat - t_plain) * 1e6 / objs,
+        "infer_ns_per_object": t_inf * 1e6 / objs,
+        "learned_ns_per_object": (t_feat - t_plain + t_inf) * 1e6 / objs,
+        "plain_finalize_ns_per_object": tr.get("shape_finalize", 0.0) * 1e6 / objs,
+        "plain_ns_per_object": t_plain * 1e6 / objs,
+        "shape_reduce_ms": tr.get("shape_reduce"), "shape_reduce_features_ms": tr.get("shape_reduce_features"),
+        "finalize_features_ms": tr.get("shape_finalize_features")}
     return res
 
 
@@ -498,8 +531,9 @@ def scaled_lt_protocol(lt, args, dev):
 
 
 def _object_features(lt, dev, m, lab, n):
-    """GPU pipeline + features of one volume: (S, R, features) as numpy and the
-    device times (ms) of the pipeline and of the features pass."""
+    """GPU pipeline with the learned features of one volume: (S, R, features)
+    as numpy, the device time (ms) of lt_measure_features and of the plain
+    lt_measure on the same volume."""
     import torch
     mt = torch.from_numpy(m).to(dev)
     labt = torch.from_numpy(lab.view(np.int32)).to(dev)
@@ -507,21 +541,19 @@ def _object_features(lt, dev, m, lab, n):
     lt2 = torch.empty_like(dt2)
     S = torch.empty(n, dtype=torch.float32, device=dev)
     R = torch.empty_like(S)
-    stats = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("volume", "n_shell", "max_lt2")}
-    stats.update({k: torch.empty(n, dtype=torch.int64, device=dev) for k in ("sum_lt", "sum_shell_lt")})
     F = torch.empty((n, lt.MLP_FEATURES), dtype=torch.float32, device=dev)
+    wsf = lt.lt_measure_features(mt, labt, n, dt2, lt2, S, R, F)
+    wsp = lt.lt_measure(mt, labt, n, dt2, lt2, S, R)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record()
-    lt.lt_edt(mt, dt2)
-    ws = lt.lt_local_thickness(dt2, labt, lt2)
-    lt.lt_shape_measures(labt, lt2, n, S, R, stats)
+    lt.lt_measure(mt, labt, n, dt2, lt2, S, R, ws=wsp)
     ev[1].record()
-    lt.lt_object_features(labt, lt2, n, stats, S, R, F)
+    lt.lt_measure_features(mt, labt, n, dt2, lt2, S, R, F, ws=wsf)
     ev[2].record()
     torch.cuda.synchronize()
-    lt.lt_workspace_status(ws)
-    return (S.cpu().numpy(), R.cpu().numpy(), F.cpu().numpy(), ev[0].elapsed_time(ev[1]),
-            ev[1].elapsed_time(ev[2]))
+    lt.lt_workspace_status(wsf)
+    return (S.cpu().numpy(), R.cpu().numpy(), F.cpu().numpy(), ev[1].elapsed_time(ev[2]),
+            ev[0].elapsed_time(ev[1]))
 
 
 def learned_c4_protocol(lt, args, dev):
@@ -572,7 +604,7 @@ def learned_c4_protocol(lt, args, dev):
     if n != n_ or labels_crc(lab) != crc_:
         raise RuntimeError("1024^3 volume differs from the one its targets were written for")
     Te = d["eval"]
-    Sg, Rg, Fg, ms_pipe, ms_feat = _object_features(lt, dev, m, lab, n)
+    Sg, Rg, Fg, ms_with, ms_plain = _object_features(lt, dev, m, lab, n)
     Ft = torch.from_numpy(Fg).to(dev)
     St = torch.from_numpy(Sg).to(dev)
     og = torch.empty(n, dtype=torch.float32, device=dev)
@@ -593,8 +625,8 @@ def learned_c4_protocol(lt, args, dev):
             "prep_s": prep_s, "eval_volume": "particles_3d_1024", "eval_objects": n_obj,
             "mae_plain": float(np.abs(Sg[ok] - Te[ok]).mean()),
             "mae_learned": float(np.abs(On[ok] - Te[ok]).mean()),
-            "per_object_ns": {"plain_pipeline": ms_pipe * 1e6 / max(1, n - 1),
-                              "features": ms_feat * 1e6 / max(1, n - 1),
+            "per_object_ns": {"plain_pipeline": ms_plain * 1e6 / max(1, n - 1),
+                              "features": (ms_with - ms_plain) * 1e6 / max(1, n - 1),
                               "inference": ms_inf * 1e6 / max(1, n - 1)},
             "target": "strict sphericity, FP64 oracle (smoothed marching tetrahedra), precomputed"}
 
@@ -801,7 +833,7 @@ def main():
         batched = measure_batch(lt, args, dev)
     learned = None
     if not args.no_learned and rank == 0:
-        learned = learned_eval(lt, args, dev)
+        learned = learned_eval(lt, args, dev, mask, labels, n_labels)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

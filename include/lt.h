@@ -209,22 +209,27 @@ lt_status lt_roundness_rescale(const float* roundness, uint32_t n, float r_min, 
 /* ---------------------------------------------------------- batched form --
  * Many volumes (2D and 3D, uneven sizes) measured as one unit of work. The
  * batch owns no device memory: `ws` (lt_batch_workspace_size bytes) holds
- * every volume's workspace. lt_batch_create checks the volumes, copies the
- * lookup tables to the device if needed and records the whole batch (for
- * each volume the kernels of lt_measure) into a CUDA graph whose volumes sit
- * on `branches` parallel branches (largest volumes first, each to the least
- * loaded branch), so small volumes run side by side. lt_batch_run launches
- * that graph on `stream` (one launch per batch); lt_batch_run_eager issues
- * the same kernels volume after volume on `stream`, the per-volume baseline.
- * lt_batch_status waits for `stream` and returns the first device-detected
- * error of any volume. lt_batch_autotune times candidate settings (branch
- * count, EDT column-tile widths, ridge z-chunk, paint grid) on the batch
- * itself, one setting at a time from the defaults, keeps the fastest and
- * rebuilds the graph; results are cached in the JSON file `cache_path`
- * (NULL: no cache) under the GPU name and the batch's shape class, and a
- * cached entry is reused without timing. The batch and its graph are host
- * objects: lt_batch_destroy releases them. Host-side calls (create,
- * autotune, destroy) are not thread-safe for the same batch. */
+ * every volume's workspace and the batch's device tables. lt_batch_create
+ * checks the volumes, copies the lookup tables to the device if needed and
+ * records the batch into a CUDA graph in which every stage of lt_measure is
+ * one kernel launch over all volumes of a group (3D volumes; 2D images):
+ * per-volume parameters and each volume's first CTA of every stage sit in a
+ * device table, and painting is one persistent grid fed by the union of all
+ * volumes' centre lists. The groups run on parallel branches; volumes with an
+ * axis over 2048 (beyond the shared-memory column tiles) run as single
+ * lt_measure chains on `branches` further branches. Results equal single
+ * lt_measure calls bit for bit. lt_batch_run launches the graph on `stream`
+ * (one launch per batch); lt_batch_run_eager issues lt_measure volume after
+ * volume on `stream`, the per-volume baseline. lt_batch_status waits for
+ * `stream` and returns the first device-detected error of any volume.
+ * lt_batch_autotune times candidate settings on the batch itself (the median
+ * of five graph launches each), one setting at a time from the defaults,
+ * keeps the fastest and re-records the graph (this waits for the device);
+ * results are cached in the JSON file `cache_path` (NULL: no cache) under the
+ * GPU name and the batch's shape class, and a cached entry is reused without
+ * timing. The batch and its graph are host objects: lt_batch_destroy
+ * releases them. Host-side calls (create, autotune, destroy) are not
+ * thread-safe for the same batch. */
 typedef struct lt_volume {
   int32_t ndim;
   uint32_t n_labels;
@@ -244,8 +249,8 @@ lt_status lt_batch_run(lt_batch* batch, void* stream);
 lt_status lt_batch_run_eager(lt_batch* batch, void* stream);
 lt_status lt_batch_status(lt_batch* batch, void* stream);
 lt_status lt_batch_autotune(lt_batch* batch, void* stream, const char* cache_path);
-/* current settings: branches, EDT y and z column-tile widths, ridge z-chunk,
- * paint CTAs per SM */
+/* current settings: EDT y and z column-tile widths, ridge z-chunk, paint CTAs
+ * per SM, largest crescent (voxels) painted in shared chunks of 32 centres */
 lt_status lt_batch_settings(const lt_batch* batch, int32_t out[5]);
 void lt_batch_destroy(lt_batch* batch);
 

@@ -14,6 +14,9 @@ everything here is this project's own definition, written plainly in FP64:
                       follows the voxel staircase and overstates a sphere's
                       area by about 27%; volume from the same mesh keeps
                       S <= 1 (isoperimetric inequality).
+  strict_sphericity_binary
+                      the same with the binary indicator's mesh (no
+                      smoothing) and V the voxel count.
   object_features     48 features per object (layout below).
   bf16                round-to-nearest-even to bfloat16.
   mlp_forward /       the 48-64-64-1 ReLU network with BF16 weights and
@@ -97,6 +100,23 @@ def strict_sphericity(labels: np.ndarray, n_labels: int) -> np.ndarray:
         w = np.asarray(which)
         ok = A > 0  # objects too thin to cross the level after smoothing have no surface
         out[w[ok]] = math.pi ** (1.0 / 3.0) * (6.0 * Vm[ok]) ** (2.0 / 3.0) / A[ok]
+    return out
+
+
+def strict_sphericity_binary(labels: np.ndarray, n_labels: int) -> np.ndarray:
+    """Eq. 1 with the area of the marching-tetrahedra surface of the
+    object's binary indicator (level 0.5, no smoothing) and V its voxel
+    count (the volume the paper's Sec. 4.1 uses). The surface follows the
+    voxel staircase, so a sphere scores about 0.8, not 1; NaN for absent
+    labels."""
+    V = np.bincount(np.asarray(labels).reshape(-1), minlength=n_labels)
+    which = [l for l in range(1, n_labels) if V[l] > 0]
+    out = np.full(n_labels, np.nan)
+    if which:
+        A, _ = mesh_area(labels, which, 0.0)
+        w = np.asarray(which)
+        ok = A > 0
+        out[w[ok]] = math.pi ** (1.0 / 3.0) * (6.0 * V[w[ok]]) ** (2.0 / 3.0) / A[ok]
     return out
 
 

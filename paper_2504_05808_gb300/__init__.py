@@ -467,8 +467,8 @@ class Batch:
     def settings(self):
         out = (ctypes.c_int32 * 5)()
         _check(lib.lt_batch_settings(self.handle, out), "lt_batch_settings")
-        return {"branches": out[0], "edt_tx_y": out[1], "edt_tx_z": out[2], "ridge_z": out[3],
-                "paint_bpsm": out[4]}
+        return {"edt_tx_y": out[0], "edt_tx_z": out[1], "ridge_z": out[2], "paint_bpsm": out[3],
+                "chunk_cres": out[4]}
 
     def close(self):
         if getattr(self, "handle", None):

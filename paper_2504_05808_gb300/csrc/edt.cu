@@ -45,13 +45,13 @@ __device__ __forceinline__ uint32_t zero_bits(const uint8_t* __restrict__ row, i
   return bits;
 }
 
-// One warp per row. Output: g per voxel (0 on background), 16 bits.
+// One warp per row (8 rows per CTA, block rb). Output: g per voxel (0 on
+// background), 16 bits.
 template <bool VEC>
-__global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict__ mask,
-                                                       uint16_t* __restrict__ out, int nx,
-                                                       uint32_t nrows) {
+__device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, uint16_t* __restrict__ out,
+                                              int nx, uint32_t nrows, uint32_t rb) {
   const int lane = threadIdx.x & 31;
-  const uint32_t row = blockIdx.x * 8u + (threadIdx.x >> 5);
+  const uint32_t row = rb * 8u + (threadIdx.x >> 5);
   if (row >= nrows) return;  // uniform per warp
   const uint8_t* mrow = mask + (size_t)row * nx;
   uint16_t* orow = out + (size_t)row * nx;
@@ -133,6 +133,25 @@ __global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict
   }
 }
 
+template <bool VEC>
+__global__ void __launch_bounds__(256) edt_rows_kernel(const uint8_t* __restrict__ mask,
+                                                       uint16_t* __restrict__ out, int nx, uint32_t nrows) {
+  edt_rows_body<VEC>(mask, out, nx, nrows, blockIdx.x);
+}
+
+// The row pass over many volumes (the 16-bit distances go to each volume's
+// workspace body).
+__global__ void __launch_bounds__(256) edt_rows_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  const uint32_t nrows = (uint32_t)p.d.ny * (uint32_t)p.d.nz;
+  uint16_t* g = reinterpret_cast<uint16_t*>(p.body);
+  if (p.d.nx % 16 == 0)
+    edt_rows_body<true>(p.mask, g, p.d.nx, nrows, blk.x);
+  else
+    edt_rows_body<false>(p.mask, g, p.d.nx, nrows, blk.x);
+}
+
 // Lower envelope at p. best starts at min(f(p), (p+1)^2, (L-p)^2), the last
 // two being the padding parabolas; the scan only visits k with k^2 < best,
 // hence k <= p and p + k < L: no bounds checks are needed. Two distances per
@@ -190,16 +209,16 @@ template <int TX>
 __host__ __device__ constexpr int cols_threads() { return TX == 32 ? 512 : 256; }
 
 template <int TX, typename In>
-__global__ void __launch_bounds__(cols_threads<TX>()) edt_cols_kernel(const In* in, uint32_t* out, int L,
-                                                                      size_t sp, int nx, size_t so, int vec) {
+__device__ __forceinline__ void edt_cols_body(const In* in, uint32_t* out, int L, size_t sp, int nx, size_t so,
+                                              int vec, uint32_t bx, uint32_t by) {
   extern __shared__ uint4 smem_raw[];
   uint32_t* tile = reinterpret_cast<uint32_t*>(smem_raw);
   constexpr int NT = cols_threads<TX>();
   constexpr int Q = TX / 4;          // 4-element pieces per tile row
   constexpr int kRows = NT / Q;      // tile rows loaded per sweep of the CTA
   constexpr int kOutRows = NT / TX;  // tile rows computed per sweep
-  const int x0 = blockIdx.x * TX;
-  const size_t off = (size_t)blockIdx.y * so + x0;
+  const int x0 = (int)bx * TX;
+  const size_t off = (size_t)by * so + x0;
   const int ncol = min(TX, nx - x0);
   {
     const int qd = threadIdx.x % Q;
@@ -223,18 +242,40 @@ __global__ void __launch_bounds__(cols_threads<TX>()) edt_cols_kernel(const In* 
   }
 }
 
+template <int TX, typename In>
+__global__ void __launch_bounds__(cols_threads<TX>()) edt_cols_kernel(const In* in, uint32_t* out, int L,
+                                                                      size_t sp, int nx, size_t so, int vec) {
+  edt_cols_body<TX, In>(in, out, L, sp, nx, so, vec, blockIdx.x, blockIdx.y);
+}
+
+// The y (AXIS 1: the 16-bit row distances of the workspace into dt2) or z
+// (AXIS 2: dt2 in place) column pass over many volumes; the dynamic shared
+// memory holds the longest column of the launch.
+template <int TX, int AXIS>
+__global__ void __launch_bounds__(cols_threads<TX>()) edt_cols_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  const Dims& d = p.d;
+  const size_t plane = (size_t)d.nx * d.ny;
+  const int vec = d.nx % 4 == 0;
+  if (AXIS == 1)
+    edt_cols_body<TX, uint16_t>(reinterpret_cast<const uint16_t*>(p.body), p.dt2, d.ny, (size_t)d.nx, d.nx, plane,
+                                vec, blk.x, blk.y);
+  else
+    edt_cols_body<TX, uint32_t>(p.dt2, p.dt2, d.nz, plane, d.nx, (size_t)d.nx, vec, blk.x, blk.y);
+}
+
 // Column pass reading `in` and writing `out` directly (axes longer than the
 // shared-memory tile allows); `in` and `out` must differ.
 template <typename In>
-__global__ void __launch_bounds__(256) edt_cols_global_kernel(const In* __restrict__ in,
-                                                              uint32_t* __restrict__ out, int L,
-                                                              size_t sp, int nx, size_t so,
-                                                              int rows_per_block) {
-  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+__device__ __forceinline__ void edt_cols_global_body(const In* __restrict__ in, uint32_t* __restrict__ out, int L,
+                                                     size_t sp, int nx, size_t so, int rows_per_block, uint32_t bx,
+                                                     uint32_t by, uint32_t bz) {
+  const int c = (int)bx * 32 + (threadIdx.x & 31);
   if (c >= nx) return;
-  const size_t off = (size_t)blockIdx.y * so + c;
+  const size_t off = (size_t)by * so + c;
   const In* col = in + off;
-  const int p0 = blockIdx.z * rows_per_block;
+  const int p0 = (int)bz * rows_per_block;
   const int p1 = min(L, p0 + rows_per_block);
   for (int p = p0 + (threadIdx.x >> 5); p < p1; p += blockDim.x >> 5) {
     uint32_t best = load1(col + (size_t)p * sp);
@@ -249,6 +290,25 @@ __global__ void __launch_bounds__(256) edt_cols_global_kernel(const In* __restri
     }
     out[off + (size_t)p * sp] = best;
   }
+}
+
+template <typename In>
+__global__ void __launch_bounds__(256) edt_cols_global_kernel(const In* __restrict__ in,
+                                                              uint32_t* __restrict__ out, int L,
+                                                              size_t sp, int nx, size_t so,
+                                                              int rows_per_block) {
+  edt_cols_global_body<In>(in, out, L, sp, nx, so, rows_per_block, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The y pass of 2D images whose columns are longer than the shared-memory
+// tiles allow, over many images (16-bit row distances into dt2).
+constexpr int kGlobalRows = 64;  // column positions per CTA of the global-memory pass
+__global__ void __launch_bounds__(256) edt_cols_global_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  const Dims& d = p.d;
+  edt_cols_global_body<uint16_t>(reinterpret_cast<const uint16_t*>(p.body), p.dt2, d.ny, (size_t)d.nx, d.nx,
+                                 (size_t)d.nx * d.ny, kGlobalRows, blk.x, blk.y, blk.z);
 }
 
 template <int TX, typename In>
@@ -289,6 +349,62 @@ cudaError_t col_pass(const char* name, const In* in, uint32_t* out, int L, size_
 }
 
 }  // namespace
+
+// ---- batched passes (see StagePlan). Column tile width for a launch whose
+// longest column is max_L: the tuned width up to 512, then 16 up to 1024, 8
+// up to 2048; 0 = the global-memory pass (2D y pass only).
+int edt_multi_tx(int max_L, int tx_small) {
+  if (max_L <= 512) return tx_small == 8 || tx_small == 16 ? tx_small : 32;
+  if (max_L <= 1024) return 16;
+  if (max_L <= 2048) return 8;
+  return 0;
+}
+
+// A volume's grid of pass 0 (rows), 1 (y columns), 2 (z columns) with tile
+// width tx (0: the global-memory y pass).
+dim3 edt_multi_grid(const Dims& d, int pass, int tx) {
+  if (pass == 0) return dim3(((uint32_t)d.ny * (uint32_t)d.nz + 7) / 8, 1, 1);
+  if (pass == 1 && tx == 0) return dim3((d.nx + 31) / 32, d.nz, (d.ny + kGlobalRows - 1) / kGlobalRows);
+  return dim3((d.nx + tx - 1) / tx, pass == 1 ? d.nz : d.ny, 1);
+}
+
+template <int TX, int AXIS>
+static cudaError_t launch_cols_multi(const MultiArgs& m, uint32_t blocks, int max_L, cudaStream_t s) {
+  const int smem = max_L * TX * 4;
+  cudaError_t e = allow_smem((const void*)edt_cols_multi_kernel<TX, AXIS>, smem);
+  if (e != cudaSuccess) return e;
+  {
+    TraceScope t(AXIS == 1 ? "edt_cols_y" : "edt_cols_z", s);
+    edt_cols_multi_kernel<TX, AXIS><<<blocks, cols_threads<TX>(), smem, s>>>(m);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t edt_multi_launch(const MultiArgs& m, uint32_t blocks, int pass, int tx, int max_L, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  if (pass == 0) {
+    {
+      TraceScope t("edt_rows_x", s);
+      edt_rows_multi_kernel<<<blocks, 256, 0, s>>>(m);
+    }
+    return cudaGetLastError();
+  }
+  if (pass == 1 && tx == 0) {
+    {
+      TraceScope t("edt_cols_y", s);
+      edt_cols_global_multi_kernel<<<blocks, 256, 0, s>>>(m);
+    }
+    return cudaGetLastError();
+  }
+  if (pass == 1) {
+    if (tx == 8) return launch_cols_multi<8, 1>(m, blocks, max_L, s);
+    if (tx == 16) return launch_cols_multi<16, 1>(m, blocks, max_L, s);
+    return launch_cols_multi<32, 1>(m, blocks, max_L, s);
+  }
+  if (tx == 8) return launch_cols_multi<8, 2>(m, blocks, max_L, s);
+  if (tx == 16) return launch_cols_multi<16, 2>(m, blocks, max_L, s);
+  return launch_cols_multi<32, 2>(m, blocks, max_L, s);
+}
 
 cudaError_t edt_prepare_device() {
   cudaError_t e = cudaSuccess;

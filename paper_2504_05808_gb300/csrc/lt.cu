@@ -293,6 +293,7 @@ static_assert(kListBuf >= kTile && kSlots == 4 && kKeptQ <= 256, "buffer, ring a
 struct RidgeWait {
   uint64_t limit_ns = kWaitNs;
   uint32_t extra_tx = 0;
+  uint32_t chunk_cres = kChunkCres;  // largest crescent of the front list (shared chunks)
 };
 
 // The record of kept centre at tile position (tx, ty) of plane zc from its
@@ -302,8 +303,8 @@ struct RidgeWait {
 template <int NDIM>
 __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3], int tx, int ty, int zc, int x0,
                                              int y0, const Dims& d, const uint32_t* mt, const uint16_t* sbase,
-                                             uint4* __restrict__ surv, WsHeader* __restrict__ hdr, bool& keepA,
-                                             bool& keepB) {
+                                             uint4* __restrict__ surv, WsHeader* __restrict__ hdr,
+                                             uint32_t chunk_cres, bool& keepA, bool& keepB) {
   // candidates: per class the largest key when it ranks above c (2 r'^2 +
   // bit > 2 r^2)
   int brn[3] = {-1, -1, -1};
@@ -376,7 +377,7 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
     rec = make_uint4(v, r2 | (code << 25), extra, 0u);
   }
   // small crescents are shared out in chunks; a big one takes a warp
-  keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= (uint32_t)kChunkCres);
+  keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= chunk_cres);
   keepB = !keepA;
   if (keepB && (NDIM == 2 || !tab)) {
     // painted row by row, written at once (these centres are rare): a big
@@ -394,29 +395,48 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
   return rec;
 }
 
-template <int NDIM, int RZ, bool TMA>
-__global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ CUtensorMap map_dt2,
-                                                       const __grid_constant__ CUtensorMap map_lab,
-                                                       const uint32_t* __restrict__ dt2,
-                                                       const uint32_t* __restrict__ labels,
-                                                       uint32_t* __restrict__ lt2, Dims d,
-                                                       uint4* __restrict__ surv,
-                                                       WsHeader* __restrict__ hdr, RidgeWait wt, int z_base,
-                                                       uint32_t* __restrict__ max_dt2, uint32_t n_labels) {
-  __shared__ __align__(128) uint32_t sD[kSlots][kSlotPitch];
-  __shared__ __align__(128) uint32_t sL[kSlots][kSlotPitch];
-  __shared__ uint4 buf[kListBuf];
-  __shared__ uint4 keptq[2][kKeptQ];   // stage 2 -> stage 3: (tile position, class keys), by plane parity
-  __shared__ uint16_t work[2][kTile];  // stage 1 -> stage 2, by plane parity
-  __shared__ __align__(8) uint64_t bar[kSlots];
-  __shared__ uint32_t cntA, cntB, baseA, baseB, flags;
+// Shared memory of one ridge CTA (declared by the kernels, so that a kernel
+// that picks the TMA or the plain-load body at run time holds it once).
+template <int NDIM>
+struct RidgeSmem {
+  __align__(128) uint32_t sD[kSlots][kSlotPitch];
+  __align__(128) uint32_t sL[kSlots][kSlotPitch];
+  uint4 buf[kListBuf];
+  uint4 keptq[2][kKeptQ];   // stage 2 -> stage 3: (tile position, class keys), by plane parity
+  uint16_t work[2][kTile];  // stage 1 -> stage 2, by plane parity
+  __align__(8) uint64_t bar[kSlots];
+  uint32_t cntA, cntB, baseA, baseB, flags;
   // list counts by plane mod 3: filled in one iteration, read in the next,
   // cleared in the one after
-  __shared__ uint32_t nwork_s[3], nkept_s[3];
-  __shared__ uint16_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 2];  // copy of g_cres_base
+  uint32_t nwork_s[3], nkept_s[3];
+  uint16_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 2];  // copy of g_cres_base
+};
+
+// One CTA of the ridge pass: column tile (blk.x, blk.y), z chunk blk.z.
+template <int NDIM, int RZ, bool TMA>
+__device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMap* map_dt2,
+                                           const CUtensorMap* map_lab, const uint32_t* __restrict__ dt2,
+                                           const uint32_t* __restrict__ labels, uint32_t* __restrict__ lt2,
+                                           const Dims& d, uint4* __restrict__ surv, WsHeader* __restrict__ hdr,
+                                           const RidgeWait& wt, int z_base, uint32_t* __restrict__ max_dt2,
+                                           uint32_t n_labels, uint3 blk) {
+  auto& sD = sm.sD;
+  auto& sL = sm.sL;
+  auto& buf = sm.buf;
+  auto& keptq = sm.keptq;
+  auto& work = sm.work;
+  auto& bar = sm.bar;
+  auto& cntA = sm.cntA;
+  auto& cntB = sm.cntB;
+  auto& baseA = sm.baseA;
+  auto& baseB = sm.baseB;
+  auto& flags = sm.flags;
+  auto& nwork_s = sm.nwork_s;
+  auto& nkept_s = sm.nkept_s;
+  auto& sbase = sm.sbase;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int z0 = NDIM == 3 ? blockIdx.z * RZ + z_base : 0;
+  const int x0 = (int)blk.x * kTX, y0 = (int)blk.y * kTY;
+  const int z0 = NDIM == 3 ? (int)blk.z * RZ + z_base : 0;
   const int z1 = NDIM == 3 ? min(d.nz, z0 + RZ) : 1;
   const size_t plane = (size_t)d.nx * d.ny;
   const uint32_t* mt = NDIM == 3 ? g_m3 : g_m2;
@@ -429,8 +449,8 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   auto issue = [&](int p) {
     const int s = slot_of(p);
     mbar_expect_tx(&bar[s], 2 * kPlaneBytes + wt.extra_tx);
-    tma_load_3d(sD[s], &map_dt2, x0 - kOX, y0 - 1, p, &bar[s]);
-    tma_load_3d(sL[s], &map_lab, x0 - kOX, y0 - 1, p, &bar[s]);
+    tma_load_3d(sD[s], map_dt2, x0 - kOX, y0 - 1, p, &bar[s]);
+    tma_load_3d(sL[s], map_lab, x0 - kOX, y0 - 1, p, &bar[s]);
   };
   auto load_plane = [&](int z) {
     const int s = slot_of(z);
@@ -597,7 +617,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           uint4 rec = make_uint4(0u, 0u, 0u, 0u);
           if (late)
             rec = make_record<NDIM>(r2, kmax, (int)(t % kTX), (int)(t / kTX), zc, x0, y0, d, mt, sbase, surv, hdr,
-                                    keepA, keepB);
+                                    wt.chunk_cres, keepA, keepB);
           append(keepA, keepB, rec);
         }
       }
@@ -617,7 +637,7 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
           const int tx = (int)(q.x % kTX), ty = (int)(q.x / kTX);
           const uint32_t r2 = D0[(ty + 1) * kBX + tx + kOX];
           const uint32_t kmax[3] = {q.y, q.z, q.w};
-          rec = make_record<NDIM>(r2, kmax, tx, ty, zr, x0, y0, d, mt, sbase, surv, hdr, keepA, keepB);
+          rec = make_record<NDIM>(r2, kmax, tx, ty, zr, x0, y0, d, mt, sbase, surv, hdr, wt.chunk_cres, keepA, keepB);
         }
         append(keepA, keepB, rec);
       }
@@ -654,6 +674,32 @@ __global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ C
   }
   if (__syncthreads_or(touch) && tid == 0) atomicOr(&hdr->touch, 1u);
   if (tid == 0 && (flags & 1u)) atomicOr(&hdr->error, ERR_LABEL_OUTSIDE_MASK);
+}
+
+template <int NDIM, int RZ, bool TMA>
+__global__ void __launch_bounds__(256) lt_ridge_kernel(const __grid_constant__ CUtensorMap map_dt2,
+                                                       const __grid_constant__ CUtensorMap map_lab,
+                                                       const uint32_t* __restrict__ dt2,
+                                                       const uint32_t* __restrict__ labels,
+                                                       uint32_t* __restrict__ lt2, Dims d,
+                                                       uint4* __restrict__ surv,
+                                                       WsHeader* __restrict__ hdr, RidgeWait wt, int z_base,
+                                                       uint32_t* __restrict__ max_dt2, uint32_t n_labels) {
+  __shared__ RidgeSmem<NDIM> sm;
+  ridge_body<NDIM, RZ, TMA>(sm, &map_dt2, &map_lab, dt2, labels, lt2, d, surv, hdr, wt, z_base, max_dt2, n_labels,
+                            make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+}
+
+// The ridge pass over many volumes (each with its own workspace: header and
+// centre records); with TMA every volume of the launch has tensor maps.
+template <int NDIM, int RZ, bool TMA>
+__global__ void __launch_bounds__(256, 5) lt_ridge_multi_kernel(MultiArgs m, RidgeWait wt) {
+  __shared__ RidgeSmem<NDIM> sm;
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  ridge_body<NDIM, RZ, TMA>(sm, reinterpret_cast<const CUtensorMap*>(p.map_dt2),
+                            reinterpret_cast<const CUtensorMap*>(p.map_lab), p.dt2, p.labels, p.lt2, p.d,
+                            reinterpret_cast<uint4*>(p.body), p.hdr, wt, 0, nullptr, 0u, blk);
 }
 
 // ---------------------------------------------------------- paint kernel
@@ -1084,81 +1130,89 @@ struct WorkGrab {
 constexpr uint32_t kChunkGrab = 8;  // phase 2 chunks per counter update, at most
 constexpr uint32_t kBigGrab = 8;    // phase 1 centres per counter update, at most
 
-// Phase 2 in 3D: chunks of 32 table centres; the lanes share the chunk's
-// crescent voxels, two per lane in flight.
-__device__ __forceinline__ void paint_table_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
-                                                   size_t sy, size_t sz, bool touch,
-                                                   const uint32_t* __restrict__ dt2,
-                                                   const uint32_t* __restrict__ labels,
-                                                   uint32_t* __restrict__ lt2, WsHeader* __restrict__ hdr,
-                                                   const PaintLut& L, uint32_t& ntab) {
+// Phase 2 in 3D: chunk ch of 32 table centres (of n in the front list);
+// the lanes share the chunk's crescent voxels, two per lane in flight.
+__device__ __forceinline__ void paint_table_chunk(const uint4* __restrict__ surv, uint32_t n, uint32_t ch,
+                                                  const Dims& d, size_t sy, size_t sz, bool touch,
+                                                  const uint32_t* __restrict__ dt2,
+                                                  const uint32_t* __restrict__ labels, uint32_t* __restrict__ lt2,
+                                                  const PaintLut& L, uint32_t& ntab) {
   __shared__ uint4 csA[8][32], csB[8][32];  // (idx, vstart, start, r2ax), (S, ex) of the chunk's centres
   __shared__ uint32_t csL[8][32];            // their labels (touch only)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t nchunks = (n + 31) / 32;
-  WorkGrab grab;
-  uint32_t ch = 0;
-  while (grab.take(&hdr->ctr_small, nchunks, kChunkGrab, ch)) {
-    const uint32_t i = ch * 32 + lane;
-    int cnt = 0;
-    TabCentre mine;
-    if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, L, mine);
-    int total;
-    const int start = warp_starts(cnt, lane, &total);
-    if (i < n) {
-      csA[w][lane] = make_uint4(mine.idx, mine.vstart, (uint32_t)start, mine.r2ax);
-      csB[w][lane] = make_uint4((uint32_t)mine.S[0], (uint32_t)mine.S[1], (uint32_t)mine.S[2], mine.ex);
-      csL[w][lane] = mine.label;
-    }
-    __syncwarp();
-    auto load = [&](int j) {
-      TabCentre c;
-      const uint4 A = csA[w][j], B = csB[w][j];
-      c.idx = A.x, c.vstart = A.y, c.start = A.z, c.r2ax = A.w;
-      c.S[0] = (int)B.x, c.S[1] = (int)B.y, c.S[2] = (int)B.z, c.ex = B.w;
-      c.label = touch ? csL[w][j] : 0u;
-      return c;
-    };
-    for (int kb = 0; kb < total; kb += 64) {
-      const int k0 = kb + lane, k1 = k0 + 32;
-      const TabCentre c0 = load(owner_lane(start, k0)), c1 = load(owner_lane(start, k1));
-      paint_tab_pair(c0, k0 - (int)c0.start, k0 < total, c1, k1 - (int)c1.start, k1 < total, d, touch, dt2, labels,
-                     lt2, ntab);
-    }
-    __syncwarp();
+  const uint32_t i = ch * 32 + lane;
+  int cnt = 0;
+  TabCentre mine;
+  if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, L, mine);
+  int total;
+  const int start = warp_starts(cnt, lane, &total);
+  if (i < n) {
+    csA[w][lane] = make_uint4(mine.idx, mine.vstart, (uint32_t)start, mine.r2ax);
+    csB[w][lane] = make_uint4((uint32_t)mine.S[0], (uint32_t)mine.S[1], (uint32_t)mine.S[2], mine.ex);
+    csL[w][lane] = mine.label;
   }
+  __syncwarp();
+  auto load = [&](int j) {
+    TabCentre c;
+    const uint4 A = csA[w][j], B = csB[w][j];
+    c.idx = A.x, c.vstart = A.y, c.start = A.z, c.r2ax = A.w;
+    c.S[0] = (int)B.x, c.S[1] = (int)B.y, c.S[2] = (int)B.z, c.ex = B.w;
+    c.label = touch ? csL[w][j] : 0u;
+    return c;
+  };
+  for (int kb = 0; kb < total; kb += 64) {
+    const int k0 = kb + lane, k1 = k0 + 32;
+    const TabCentre c0 = load(owner_lane(start, k0)), c1 = load(owner_lane(start, k1));
+    paint_tab_pair(c0, k0 - (int)c0.start, k0 < total, c1, k1 - (int)c1.start, k1 < total, d, touch, dt2, labels,
+                   lt2, ntab);
+  }
+  __syncwarp();
 }
 
-// Phase 2 in 2D: chunks of 32 centres; the lanes share the chunk's row
+// Phase 2 in 2D: chunk ch of 32 centres; the lanes share the chunk's row
 // segments.
-__device__ __forceinline__ void paint_row_chunks(const uint4* __restrict__ surv, uint32_t n, const Dims& d,
-                                                 size_t sy, size_t sz, bool touch,
-                                                 const uint32_t* __restrict__ dt2,
-                                                 const uint32_t* __restrict__ labels,
-                                                 uint32_t* __restrict__ lt2, WsHeader* __restrict__ hdr,
-                                                 uint32_t& nupd) {
+__device__ __forceinline__ void paint_row_chunk(const uint4* __restrict__ surv, uint32_t n, uint32_t ch,
+                                                const Dims& d, size_t sy, size_t sz, bool touch,
+                                                const uint32_t* __restrict__ dt2, const uint32_t* __restrict__ labels,
+                                                uint32_t* __restrict__ lt2, uint32_t& nupd) {
   __shared__ Centre cs[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t nchunks = (n + 31) / 32;
-  WorkGrab grab;
-  uint32_t ch = 0;
-  while (grab.take(&hdr->ctr_small, nchunks, 1u, ch)) {  // one chunk at a time: 2D chunks vary most in cost
-    const uint32_t i = ch * 32 + lane;
-    int cnt = 0;
-    if (i < n) cnt = make_centre<2>(surv[i], d, sy, sz, touch, dt2, labels, cs[w][lane]);
-    int total;
-    const int start = warp_starts(cnt, lane, &total);
-    if (i < n) cs[w][lane].start = start;
-    __syncwarp();
-    for (int kb = 0; kb < total; kb += 32) {
-      const int k = kb + lane;
-      const int j = owner_lane(start, k);
-      if (k < total) {
-        const Centre& c = cs[w][j];
-        paint_row_item<2>(c, k - c.start, d, sy, sz, touch, dt2, labels, lt2, nupd);
-      }
+  const uint32_t i = ch * 32 + lane;
+  int cnt = 0;
+  if (i < n) cnt = make_centre<2>(surv[i], d, sy, sz, touch, dt2, labels, cs[w][lane]);
+  int total;
+  const int start = warp_starts(cnt, lane, &total);
+  if (i < n) cs[w][lane].start = start;
+  __syncwarp();
+  for (int kb = 0; kb < total; kb += 32) {
+    const int k = kb + lane;
+    const int j = owner_lane(start, k);
+    if (k < total) {
+      const Centre& c = cs[w][j];
+      paint_row_item<2>(c, k - c.start, d, sy, sz, touch, dt2, labels, lt2, nupd);
     }
-    __syncwarp();
+  }
+  __syncwarp();
+}
+
+// Phase 1: one back-list record, one warp (big table crescent, or a part of
+// a centre painted row by row).
+template <int NDIM>
+__device__ __forceinline__ void paint_big(const uint4& rec, const Dims& d, size_t sy, size_t sz, bool touch,
+                                          const uint32_t* __restrict__ dt2, const uint32_t* __restrict__ labels,
+                                          uint32_t* __restrict__ lt2, const PaintLut& lut, uint32_t& nupd,
+                                          uint32_t& ntab) {
+  const int lane = threadIdx.x & 31;
+  if (NDIM == 3 && (rec.z & kTableRecord)) {
+    TabCentre c;
+    const int items = make_tab_centre(rec, sy, sz, touch, labels, lut, c);
+    for (int k = lane; k < items; k += 64)
+      paint_tab_pair(c, k, true, c, k + 32, k + 32 < items, d, touch, dt2, labels, lt2, ntab);
+  } else {
+    Centre c;
+    make_centre<NDIM>(rec, d, sy, sz, touch, dt2, labels, c);
+    paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFu), max(1, (int)(rec.w >> 8)), d, sy, sz, touch, dt2, labels, lt2,
+                            lut, nupd);
   }
 }
 
@@ -1188,25 +1242,21 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   {
     WorkGrab grab;
     uint32_t b = 0;
-    while (grab.take(&hdr->ctr_big, nbig, kBigGrab, b)) {
-      const uint4 rec = surv[record_capacity(d.n) - 1 - b];
-      if (NDIM == 3 && (rec.z & kTableRecord)) {
-        TabCentre c;
-        const int items = make_tab_centre(rec, sy, sz, touch, labels, lut, c);
-        for (int k = lane; k < items; k += 64)
-          paint_tab_pair(c, k, true, c, k + 32, k + 32 < items, d, touch, dt2, labels, lt2, ntab);
-      } else {
-        Centre c;
-        make_centre<NDIM>(rec, d, sy, sz, touch, dt2, labels, c);
-        paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFu), max(1, (int)(rec.w >> 8)), d, sy, sz, touch, dt2,
-                                labels, lt2, lut, nupd);
-      }
+    while (grab.take(&hdr->ctr_big, nbig, kBigGrab, b))
+      paint_big<NDIM>(surv[record_capacity(d.n) - 1 - b], d, sy, sz, touch, dt2, labels, lt2, lut, nupd, ntab);
+  }
+  {
+    const uint32_t nchunks = (n + 31) / 32;
+    WorkGrab grab;
+    uint32_t ch = 0;
+    // 2D chunks vary most in cost: one at a time
+    while (grab.take(&hdr->ctr_small, nchunks, NDIM == 3 ? kChunkGrab : 1u, ch)) {
+      if (NDIM == 3)
+        paint_table_chunk(surv, n, ch, d, sy, sz, touch, dt2, labels, lt2, lut, ntab);
+      else
+        paint_row_chunk(surv, n, ch, d, sy, sz, touch, dt2, labels, lt2, nupd);
     }
   }
-  if (NDIM == 3)
-    paint_table_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, lut, ntab);
-  else
-    paint_row_chunks(surv, n, d, sy, sz, touch, dt2, labels, lt2, hdr, nupd);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     nupd += __shfl_xor_sync(kFull, nupd, o);
@@ -1215,6 +1265,98 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   if (lane == 0 && nupd + ntab) {
     atomicAdd(&hdr->n_updates, (unsigned long long)(nupd + ntab));
     atomicAdd(&hdr->n_table_updates, (unsigned long long)ntab);
+  }
+}
+
+// Painting of many volumes in one persistent grid: the back lists of all
+// volumes, then the front lists' chunks, each from one counter of `ctr`
+// (ctr[0] back items, ctr[1] chunks; zero before the launch). Every CTA
+// first takes the volumes' list lengths (from their headers, after the
+// ridge pass) and their prefix sums, so that an item maps to its volume.
+template <int NDIM>
+__global__ void __launch_bounds__(256) lt_paint_multi_kernel(MultiArgs m, uint32_t* __restrict__ ctr) {
+  __shared__ uint32_t big0[kMaxBatchVols + 1], chunk0[kMaxBatchVols + 1];
+  __shared__ uint32_t wsum[2][8];
+  __shared__ PaintLut lut;
+  init_paint_lut(lut);
+  // block-wide exclusive scans of the per-volume item counts (nvol <= 256)
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t nb = 0, nc = 0;
+  if (tid < m.nvol) {
+    const WsHeader* h = m.vols[tid].hdr;
+    nb = *(volatile const uint32_t*)&h->n_big;
+    nc = (*(volatile const uint32_t*)&h->n_surv + 31u) / 32u;
+  }
+  uint32_t ib = nb, ic = nc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t tb = __shfl_up_sync(kFull, ib, o), tc = __shfl_up_sync(kFull, ic, o);
+    if (lane >= o) {
+      ib += tb;
+      ic += tc;
+    }
+  }
+  if (lane == 31) {
+    wsum[0][w] = ib;
+    wsum[1][w] = ic;
+  }
+  __syncthreads();
+  uint32_t ob = 0, oc = 0;
+  for (int k = 0; k < w; ++k) {
+    ob += wsum[0][k];
+    oc += wsum[1][k];
+  }
+  if (tid < m.nvol) {
+    big0[tid] = ob + ib - nb;
+    chunk0[tid] = oc + ic - nc;
+  }
+  if (tid == 0) {
+    uint32_t tb = 0, tc = 0;
+    for (int k = 0; k < 8; ++k) {
+      tb += wsum[0][k];
+      tc += wsum[1][k];
+    }
+    big0[m.nvol] = tb;
+    chunk0[m.nvol] = tc;
+  }
+  __syncthreads();
+  auto vol_of = [&](const uint32_t* start, uint32_t item) {
+    int lo = 0, hi = m.nvol;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (start[mid] <= item) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  };
+  uint32_t nupd = 0, ntab = 0;
+  {
+    WorkGrab grab;
+    uint32_t b = 0;
+    while (grab.take(&ctr[0], big0[m.nvol], kBigGrab, b)) {
+      const int v = vol_of(big0, b);
+      const VolParams& p = m.vols[v];
+      const bool touch = *(volatile const uint32_t*)&p.hdr->touch != 0;
+      const uint4* surv = reinterpret_cast<const uint4*>(p.body);
+      paint_big<NDIM>(surv[record_capacity(p.d.n) - 1 - (b - big0[v])], p.d, (size_t)p.d.nx,
+                      (size_t)p.d.nx * p.d.ny, touch, p.dt2, p.labels, p.lt2, lut, nupd, ntab);
+    }
+  }
+  {
+    WorkGrab grab;
+    uint32_t ch = 0;
+    while (grab.take(&ctr[1], chunk0[m.nvol], NDIM == 3 ? kChunkGrab : 1u, ch)) {
+      const int v = vol_of(chunk0, ch);
+      const VolParams& p = m.vols[v];
+      const bool touch = *(volatile const uint32_t*)&p.hdr->touch != 0;
+      const uint4* surv = reinterpret_cast<const uint4*>(p.body);
+      const uint32_t n = *(volatile const uint32_t*)&p.hdr->n_surv;
+      const size_t sy = (size_t)p.d.nx, sz = (size_t)p.d.nx * p.d.ny;
+      if (NDIM == 3)
+        paint_table_chunk(surv, n, ch - chunk0[v], p.d, sy, sz, touch, p.dt2, p.labels, p.lt2, lut, ntab);
+      else
+        paint_row_chunk(surv, n, ch - chunk0[v], p.d, sy, sz, touch, p.dt2, p.labels, p.lt2, nupd);
+    }
   }
 }
 
@@ -1323,7 +1465,8 @@ cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_
   const int zb = c_lo * rz;
   {
     TraceScope t("lt_ridge", s);
-    const RidgeWait wt;
+    RidgeWait wt;
+    wt.chunk_cres = (uint32_t)std::max(1, std::min(1024, tu.chunk_cres));
     if (d.ndim == 2)
       launch_ridge<2, 16>(tma, grid, s, md, ml, dt2, labels, lt2, d, surv, hdr, wt, 0, max_dt2, n_labels);
     else if (rz == 8)
@@ -1368,6 +1511,73 @@ cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_
       lt_paint_kernel<3><<<pblocks, 256, 0, s>>>(surv, dt2, labels, lt2, d, hdr);
     else
       lt_paint_kernel<2><<<pblocks, 256, 0, s>>>(surv, dt2, labels, lt2, d, hdr);
+  }
+  return cudaGetLastError();
+}
+
+// ---- batched ridge and paint (see StagePlan)
+dim3 lt_ridge_grid(const Dims& d, const Tuning& tu) {
+  const int rz = ridge_chunk(tu);
+  return dim3((d.nx + kTX - 1) / kTX, (d.ny + kTY - 1) / kTY, d.ndim == 3 ? (d.nz + rz - 1) / rz : 1);
+}
+
+bool lt_ridge_tensor_maps(void* map_dt2, void* map_lab, const uint32_t* dt2, const uint32_t* labels, const Dims& d) {
+  return d.nx % 4 == 0 &&
+         make_tensor_map_u32_3d(reinterpret_cast<CUtensorMap*>(map_dt2), dt2, d.nx, d.ny, d.nz, kBX, kBY) &&
+         make_tensor_map_u32_3d(reinterpret_cast<CUtensorMap*>(map_lab), labels, d.nx, d.ny, d.nz, kBX, kBY);
+}
+
+template <bool TMA>
+static void ridge_multi(const MultiArgs& m, uint32_t blocks, int ndim, int rz, const RidgeWait& wt, cudaStream_t s) {
+  if (ndim == 2)
+    lt_ridge_multi_kernel<2, 16, TMA><<<blocks, 256, 0, s>>>(m, wt);
+  else if (rz == 8)
+    lt_ridge_multi_kernel<3, 8, TMA><<<blocks, 256, 0, s>>>(m, wt);
+  else if (rz == 32)
+    lt_ridge_multi_kernel<3, 32, TMA><<<blocks, 256, 0, s>>>(m, wt);
+  else
+    lt_ridge_multi_kernel<3, 16, TMA><<<blocks, 256, 0, s>>>(m, wt);
+}
+
+cudaError_t lt_ridge_multi_launch(const MultiArgs& m, uint32_t blocks, int ndim, bool tma, const Tuning& tu,
+                                  cudaStream_t s) {
+  cudaError_t e = ensure_tables();
+  if (e != cudaSuccess || blocks == 0) return e;
+  RidgeWait wt;
+  wt.chunk_cres = (uint32_t)std::max(1, std::min(1024, tu.chunk_cres));
+  {
+    TraceScope t("lt_ridge", s);
+    if (tma)
+      ridge_multi<true>(m, blocks, ndim, ridge_chunk(tu), wt, s);
+    else
+      ridge_multi<false>(m, blocks, ndim, ridge_chunk(tu), wt, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t lt_paint_multi_launch(const MultiArgs& m, int ndim, uint32_t* ctr, const Tuning& tu, cudaStream_t s) {
+  static const int fit[2] = {[] {
+                               int v = 0;
+                               if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lt_paint_multi_kernel<2>, 256,
+                                                                                 0) != cudaSuccess || v < 1)
+                                 v = 1;
+                               return v;
+                             }(),
+                             [] {
+                               int v = 0;
+                               if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lt_paint_multi_kernel<3>, 256,
+                                                                                 0) != cudaSuccess || v < 1)
+                                 v = 1;
+                               return v;
+                             }()};
+  const int bps = std::min(tu.paint_blocks_per_sm > 0 ? tu.paint_blocks_per_sm : 8, fit[ndim == 3]);
+  const unsigned blocks = (unsigned)(sm_count() * bps);
+  {
+    TraceScope t("lt_paint", s);
+    if (ndim == 3)
+      lt_paint_multi_kernel<3><<<blocks, 256, 0, s>>>(m, ctr);
+    else
+      lt_paint_multi_kernel<2><<<blocks, 256, 0, s>>>(m, ctr);
   }
   return cudaGetLastError();
 }

@@ -36,7 +36,7 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 enum : uint32_t { ERR_LABEL_RANGE = 1u, ERR_LABEL_OUTSIDE_MASK = 2u, ERR_TIMEOUT = 4u };
 
 constexpr size_t kAlign = 256;
-constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+__host__ __device__ constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Floor square root of v < 2^24: IEEE-rounded single-precision square root
 // of an exactly representable integer is within one of the floor; fix it.
@@ -56,6 +56,49 @@ struct ShapeAcc {
   unsigned long long* sum_shell_lt;
 };
 
+// ---- stage-major batches: one launch of a stage covers many volumes ----
+// Per volume, its parameters in device memory; per stage, the first CTA of
+// every volume in the launch's one-dimensional grid and the volume's own
+// grid extents, so that a CTA finds its volume by binary search and its
+// block coordinates within that volume's grid.
+constexpr int kMaxBatchVols = 256;
+struct VolParams {
+  Dims d;
+  uint32_t n_labels;
+  const uint8_t* mask;
+  const uint32_t* labels;
+  uint32_t* dt2;
+  uint32_t* lt2;
+  float* S;
+  float* R;
+  WsHeader* hdr;        // the volume's workspace header
+  char* body;           // and the scratch after it
+  const void* map_dt2;  // TMA tensor maps (CUtensorMap, global memory), null without TMA
+  const void* map_lab;
+};
+struct StagePlan {
+  uint32_t start[kMaxBatchVols + 1];  // first CTA of volume v; start[n] = the launch's CTAs
+  uint32_t gx[kMaxBatchVols], gy[kMaxBatchVols];
+};
+struct MultiArgs {
+  const VolParams* vols;
+  const StagePlan* plan;
+  int nvol;
+};
+// The volume of CTA b and its block coordinates within that volume's grid.
+__device__ __forceinline__ int find_volume(const MultiArgs& m, uint32_t b, uint3& blk) {
+  int lo = 0, hi = m.nvol;  // start[lo] <= b < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&m.plan->start[mid]) <= b) lo = mid;
+    else hi = mid;
+  }
+  const uint32_t local = b - __ldg(&m.plan->start[lo]);
+  const uint32_t gx = __ldg(&m.plan->gx[lo]), gy = __ldg(&m.plan->gy[lo]);
+  blk = make_uint3(local % gx, local / gx % gy, local / (gx * gy));
+  return lo;
+}
+
 // Launch parameters the batch autotuner may change (defaults: single calls).
 // Defaults: the autotuner's choice for the 512^3 particle volume on GB300.
 struct Tuning {
@@ -63,6 +106,7 @@ struct Tuning {
   int edt_tx_z = 32;            // and of the z pass (32: whole 128-byte tile rows, 512 threads)
   int ridge_z = 32;             // z planes per ridge CTA (8, 16 or 32)
   int paint_blocks_per_sm = 6;  // persistent paint grid, CTAs per SM
+  int chunk_cres = 64;          // largest crescent painted in shared chunks (bigger: a warp each)
 };
 
 // ---- host launchers (each returns cudaSuccess or the launch error) ----
@@ -72,6 +116,11 @@ cudaError_t edt_prepare_device();  // kernel attributes; call before capture
 // passes: 1 = x and y, 2 = z (on dt2 in place), 3 = all
 cudaError_t edt_launch(const uint8_t* mask, uint32_t* dt2, const Dims& d, void* ws, cudaStream_t s,
                        const Tuning& tu = Tuning(), int passes = 3);
+// batched EDT passes (pass 0 rows, 1 y columns, 2 z columns; tx 0 = the
+// global-memory y pass of long 2D columns)
+int edt_multi_tx(int max_L, int tx_small);
+dim3 edt_multi_grid(const Dims& d, int pass, int tx);
+cudaError_t edt_multi_launch(const MultiArgs& m, uint32_t blocks, int pass, int tx, int max_L, cudaStream_t s);
 // lt.cu
 size_t lt_workspace_bytes(const Dims& d);
 cudaError_t lt_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
@@ -87,6 +136,14 @@ cudaError_t lt_ridge_launch(const uint32_t* dt2, const uint32_t* labels, uint32_
                             uint32_t* max_dt2 = nullptr, uint32_t n_labels = 0);
 cudaError_t lt_paint_launch(const uint32_t* dt2, const uint32_t* labels, uint32_t* lt2, const Dims& d,
                             WsHeader* hdr, void* body, cudaStream_t s, const Tuning& tu);
+// batched ridge and paint: a volume's ridge grid; its two TMA tensor maps
+// (CUtensorMap, 128 bytes each, written to host memory; false without TMA);
+// the launches (ctr: two zeroed work counters of the persistent paint grid)
+dim3 lt_ridge_grid(const Dims& d, const Tuning& tu);
+bool lt_ridge_tensor_maps(void* map_dt2, void* map_lab, const uint32_t* dt2, const uint32_t* labels, const Dims& d);
+cudaError_t lt_ridge_multi_launch(const MultiArgs& m, uint32_t blocks, int ndim, bool tma, const Tuning& tu,
+                                  cudaStream_t s);
+cudaError_t lt_paint_multi_launch(const MultiArgs& m, int ndim, uint32_t* ctr, const Tuning& tu, cudaStream_t s);
 // timeout self-test of the ridge kernel's bounded waits (see lt.h)
 size_t ridge_selftest_bytes();
 cudaError_t ridge_selftest_launch(void* ws, cudaStream_t s);
@@ -120,6 +177,11 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
                          const Dims& d, WsHeader* hdr, void* body, float* S, float* R,
                          const lt_object_stats* stats, cudaStream_t s, uint32_t min_lt2 = 0);
 
+// batched shape stage: a volume's grid for kind 0 (reduction, 4-voxel
+// vectors: rows of a multiple of 4 voxels), 1 (one-voxel reduction), 2
+// (finalize), 3 (clear the workspace header), 4 (clear the accumulators)
+dim3 shape_multi_grid(const Dims& d, uint32_t n_labels, int kind);
+cudaError_t shape_multi_launch(const MultiArgs& m, uint32_t blocks, int kind, int ndim, cudaStream_t s);
 // the shape stage with the learned features in the same pass over the
 // volume: per-object histograms of LT / M (M^2 = ref_max[label], the
 // object's largest LT2) next to the sums, then S, R, features [n][48]

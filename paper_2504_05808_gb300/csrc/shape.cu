@@ -23,6 +23,31 @@
 #include "lt_internal.cuh"
 
 namespace ltk {
+
+// Accumulator bytes for n labels: three uint32 and two uint64 arrays, each
+// starting on a kAlign boundary (the layout of acc_layout below).
+__host__ __device__ constexpr size_t acc_bytes(uint32_t n) {
+  return 3 * align_up((size_t)n * 4) + 2 * align_up((size_t)n * 8);
+}
+
+// Per-object accumulators at the start of a shape workspace body: volume,
+// n_shell, max LT2 (uint32), sum LT, sum shell LT (uint64), each array
+// starting on a kAlign boundary.
+__host__ __device__ inline ShapeAcc acc_layout(void* body, uint32_t n_labels) {
+  char* p = reinterpret_cast<char*>(body);
+  ShapeAcc acc;
+  acc.volume = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.n_shell = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.max_lt2 = reinterpret_cast<uint32_t*>(p);
+  p += align_up((size_t)n_labels * 4);
+  acc.sum_lt = reinterpret_cast<unsigned long long*>(p);
+  p += align_up((size_t)n_labels * 8);
+  acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
+  return acc;
+}
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -39,14 +64,13 @@ __device__ __forceinline__ uint32_t obj_label(const uint32_t* __restrict__ label
 }
 
 template <int NDIM, bool FILTER>
-__global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __restrict__ labels,
-                                                           const uint32_t* __restrict__ lt2, Dims d,
-                                                           uint32_t n_labels, ShapeAcc acc,
-                                                           WsHeader* __restrict__ hdr, uint32_t min_lt2,
-                                                           int z_lo) {
+__device__ __forceinline__ void shape_reduce_body(const uint32_t* __restrict__ labels,
+                                                  const uint32_t* __restrict__ lt2, const Dims& d, uint32_t n_labels,
+                                                  const ShapeAcc& acc, WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                  int z_lo, uint3 blk) {
   const int lane = threadIdx.x & 31;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z + z_lo;
+  const int x = (int)blk.x * blockDim.x + threadIdx.x;
+  const int y = (int)blk.y, z = (int)blk.z + z_lo;
   const bool in = x < d.nx;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x : 0;
@@ -143,6 +167,16 @@ __device__ __forceinline__ void warp_uniform_sums(uint32_t& pk, uint32_t& mx, un
   qs = ((unsigned long long)sh << 16) + sl;
 }
 
+template <int NDIM, bool FILTER>
+__global__ void __launch_bounds__(256) shape_reduce_kernel(const uint32_t* __restrict__ labels,
+                                                           const uint32_t* __restrict__ lt2, Dims d,
+                                                           uint32_t n_labels, ShapeAcc acc,
+                                                           WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                           int z_lo) {
+  shape_reduce_body<NDIM, FILTER>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo,
+                                  make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+}
+
 // Vector form for nx % 4 == 0: a thread covers 4 consecutive voxels of a
 // row (16-byte loads of labels, LT2 and the neighbouring rows), adds the
 // voxels of its first nonzero label locally (voxels of another nonzero label
@@ -155,15 +189,14 @@ __device__ __forceinline__ void warp_uniform_sums(uint32_t& pk, uint32_t& mx, un
 // LT2); equal (label, shell, bin) keys of consecutive voxels are counted
 // together, then runs of equal keys across the warp.
 template <int NDIM, bool FILTER, bool HIST>
-__global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
-                                                            const uint32_t* __restrict__ lt2, Dims d,
-                                                            uint32_t n_labels, ShapeAcc acc,
-                                                            WsHeader* __restrict__ hdr, uint32_t min_lt2,
-                                                            int z_lo, const uint32_t* __restrict__ ref_max,
-                                                            uint32_t* __restrict__ hist) {
+__device__ __forceinline__ void shape_reduce4_body(const uint32_t* __restrict__ labels,
+                                                   const uint32_t* __restrict__ lt2, const Dims& d, uint32_t n_labels,
+                                                   const ShapeAcc& acc, WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                   int z_lo, const uint32_t* __restrict__ ref_max,
+                                                   uint32_t* __restrict__ hist, uint3 blk) {
   const int lane = threadIdx.x & 31;
-  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z + z_lo;
+  const int x0 = 4 * ((int)blk.x * blockDim.x + threadIdx.x);
+  const int y = (int)blk.y * blockDim.y + threadIdx.y, z = (int)blk.z + z_lo;
   const bool in = x0 < d.nx && y < d.ny;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const size_t v = in ? (size_t)z * sz + (size_t)y * sy + x0 : 0;
@@ -325,6 +358,32 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
   }
 }
 
+template <int NDIM, bool FILTER, bool HIST>
+__global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __restrict__ labels,
+                                                            const uint32_t* __restrict__ lt2, Dims d,
+                                                            uint32_t n_labels, ShapeAcc acc,
+                                                            WsHeader* __restrict__ hdr, uint32_t min_lt2,
+                                                            int z_lo, const uint32_t* __restrict__ ref_max,
+                                                            uint32_t* __restrict__ hist) {
+  shape_reduce4_body<NDIM, FILTER, HIST>(labels, lt2, d, n_labels, acc, hdr, min_lt2, z_lo, ref_max, hist,
+                                         make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+}
+
+// The shape reduction over many volumes (each volume's accumulators at the
+// start of its workspace body): VEC4 with the 64 x 4 blocks of the vector
+// form (rows of a multiple of 4 voxels), else the one-voxel form.
+template <int NDIM, bool VEC4>
+__global__ void __launch_bounds__(256) shape_reduce_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  const ShapeAcc acc = acc_layout(p.body, p.n_labels);
+  if (VEC4)
+    shape_reduce4_body<NDIM, false, false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0u, 0, nullptr, nullptr,
+                                           blk);
+  else
+    shape_reduce_body<NDIM, false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0u, 0, blk);
+}
+
 __device__ double spheroid_area(double a, double c) {
   const double pi = 3.141592653589793;
   if (c == a) return 4.0 * pi * a * a;
@@ -337,10 +396,10 @@ __device__ double spheroid_area(double a, double c) {
 }
 
 template <int NDIM>
-__global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __restrict__ S,
-                                      float* __restrict__ R, lt_object_stats st,
-                                      const uint32_t* __restrict__ hist, float* __restrict__ F) {
-  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void shape_finalize_body(const ShapeAcc& acc, uint32_t n_labels, float* __restrict__ S,
+                                                    float* __restrict__ R, const lt_object_stats& st,
+                                                    const uint32_t* __restrict__ hist, float* __restrict__ F,
+                                                    uint32_t l) {
   if (l >= n_labels) return;
   const uint32_t V = l ? acc.volume[l] : 0u;
   const uint32_t ns = l ? acc.n_shell[l] : 0u;
@@ -394,6 +453,34 @@ __global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __
   }
 }
 
+template <int NDIM>
+__global__ void shape_finalize_kernel(ShapeAcc acc, uint32_t n_labels, float* __restrict__ S,
+                                      float* __restrict__ R, lt_object_stats st,
+                                      const uint32_t* __restrict__ hist, float* __restrict__ F) {
+  shape_finalize_body<NDIM>(acc, n_labels, S, R, st, hist, F, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <int NDIM>
+__global__ void shape_finalize_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  const lt_object_stats st = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  shape_finalize_body<NDIM>(acc_layout(p.body, p.n_labels), p.n_labels, p.S, p.R, st, nullptr, nullptr,
+                            blk.x * blockDim.x + threadIdx.x);
+}
+
+// Zeroes every volume's workspace header (WHAT 0) or shape accumulators
+// (WHAT 1), 16 bytes per thread.
+template <int WHAT>
+__global__ void __launch_bounds__(256) clear_multi_kernel(MultiArgs m) {
+  uint3 blk;
+  const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
+  char* base = WHAT == 0 ? reinterpret_cast<char*>(p.hdr) : p.body;
+  const size_t bytes = WHAT == 0 ? sizeof(WsHeader) : acc_bytes(p.n_labels);
+  const size_t i = ((size_t)blk.x * blockDim.x + threadIdx.x) * 16;
+  if (i < bytes) *reinterpret_cast<uint4*>(base + i) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Roundness mapped to 0-1 with the reported minimum (Sec. 6.1). Step 1:
 // the smallest finite R over [0, n) by warp minima and one atomic per warp
 // (R > 0, so the float bits order like the values). Step 2: the map.
@@ -438,11 +525,6 @@ cudaError_t rescale_launch(const float* R, uint32_t n, float r_min, uint32_t* sc
   return cudaGetLastError();
 }
 
-// Accumulator bytes for n labels: three uint32 and two uint64 arrays, each
-// starting on a kAlign boundary (the layout of acc_layout below).
-constexpr size_t acc_bytes(uint32_t n) {
-  return 3 * align_up((size_t)n * 4) + 2 * align_up((size_t)n * 8);
-}
 
 size_t shape_workspace_bytes(uint32_t n_labels) { return acc_bytes(n_labels); }
 
@@ -461,20 +543,6 @@ void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_label
   }
 }
 
-ShapeAcc acc_layout(void* body, uint32_t n_labels) {
-  char* p = reinterpret_cast<char*>(body);
-  ShapeAcc acc;
-  acc.volume = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)n_labels * 4);
-  acc.n_shell = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)n_labels * 4);
-  acc.max_lt2 = reinterpret_cast<uint32_t*>(p);
-  p += align_up((size_t)n_labels * 4);
-  acc.sum_lt = reinterpret_cast<unsigned long long*>(p);
-  p += align_up((size_t)n_labels * 8);
-  acc.sum_shell_lt = reinterpret_cast<unsigned long long*>(p);
-  return acc;
-}
 
 cudaError_t shape_clear(void* body, uint32_t n_labels, cudaStream_t s) {
   return cudaMemsetAsync(body, 0, acc_bytes(n_labels), s);
@@ -520,6 +588,47 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
   if (e == cudaSuccess) e = shape_accumulate(labels, lt2, n_labels, d, hdr, body, 0, d.nz, s, min_lt2);
   if (e == cudaSuccess) e = shape_finalize(d.ndim, n_labels, body, S, R, stats, s);
   return e;
+}
+
+// ---- batched shape stage (see StagePlan). Kinds: 0 reduction with
+// 4-voxel vectors, 1 one-voxel reduction, 2 finalize, 3 clear headers, 4
+// clear accumulators.
+dim3 shape_multi_grid(const Dims& d, uint32_t n_labels, int kind) {
+  switch (kind) {
+    case 0: return dim3((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    case 1: return dim3((d.nx + 255) / 256, d.ny, d.nz);
+    case 2: return dim3((n_labels + 255) / 256, 1, 1);
+    case 3: return dim3(1, 1, 1);
+    default: return dim3((unsigned)((acc_bytes(n_labels) + 4095) / 4096), 1, 1);
+  }
+}
+
+cudaError_t shape_multi_launch(const MultiArgs& m, uint32_t blocks, int kind, int ndim, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  if (kind == 0) {
+    TraceScope t("shape_reduce", s);
+    if (ndim == 3)
+      shape_reduce_multi_kernel<3, true><<<blocks, dim3(64, 4), 0, s>>>(m);
+    else
+      shape_reduce_multi_kernel<2, true><<<blocks, dim3(64, 4), 0, s>>>(m);
+  } else if (kind == 1) {
+    TraceScope t("shape_reduce", s);
+    if (ndim == 3)
+      shape_reduce_multi_kernel<3, false><<<blocks, 256, 0, s>>>(m);
+    else
+      shape_reduce_multi_kernel<2, false><<<blocks, 256, 0, s>>>(m);
+  } else if (kind == 2) {
+    TraceScope t("shape_finalize", s);
+    if (ndim == 3)
+      shape_finalize_multi_kernel<3><<<blocks, 256, 0, s>>>(m);
+    else
+      shape_finalize_multi_kernel<2><<<blocks, 256, 0, s>>>(m);
+  } else if (kind == 3) {
+    clear_multi_kernel<0><<<blocks, 256, 0, s>>>(m);
+  } else {
+    clear_multi_kernel<1><<<blocks, 256, 0, s>>>(m);
+  }
+  return cudaGetLastError();
 }
 
 size_t shape_features_bytes(uint32_t n_labels) { return acc_bytes(n_labels) + align_up((size_t)n_labels * 32 * 4); }

@@ -8,8 +8,12 @@ oracle/ and the seeded generators in synth/, and writes plain numbers that
 bench.py reads, so the measurement never runs the oracle itself.
 
   python tests/golden/make_strict_targets.py bench
-      the six 160^3 training volumes of bench.py's learned leg
-      -> tests/golden/strict_sphericity_training.txt
+      the learned leg of bench.py: BENCH_VOLUMES volumes of
+      synth.training_particles(320, seed), seeds from BENCH_SEED0 (the first
+      BENCH_TRAIN for training, ~20 k particles; the rest held out, ~100 k),
+      both target definitions (smoothed mesh with its enclosed volume, and
+      binary-indicator mesh with the voxel count)
+      -> tests/golden/strict_sphericity_bench.txt
   python tests/golden/make_strict_targets.py c4 --out FILE.npz [--train-volumes N] [--edge E]
       N training volumes of edge E (about 2,440 particles each at E = 320;
       82 volumes give ~200 k particles) and the 1024^3 volume of ~1 M
@@ -37,8 +41,8 @@ import oracle  # noqa: E402
 import oracle.learned as L  # noqa: E402
 import synth  # noqa: E402
 
-BENCH_FILE = os.path.join(HERE, "strict_sphericity_training.txt")
-BENCH_EDGE, BENCH_SEEDS = 160, tuple(range(100, 106))
+BENCH_FILE = os.path.join(HERE, "strict_sphericity_bench.txt")
+BENCH_EDGE, BENCH_SEED0, BENCH_VOLUMES, BENCH_TRAIN = 320, 2000, 62, 10
 
 
 def crc(labels: np.ndarray) -> int:
@@ -49,39 +53,43 @@ def targets(labels: np.ndarray, n: int) -> np.ndarray:
     return L.strict_sphericity(labels, n)
 
 
+def _fmt(T: np.ndarray) -> str:
+    return " ".join("nan" if not np.isfinite(t) else f"{t:.7g}" for t in T[1:])
+
+
 def write_bench() -> None:
-    lines = ["# strict sphericity (FP64 oracle: smoothed marching-tetrahedra mesh, Eq. 1)",
-             f"# of synth.training_particles({BENCH_EDGE}, seed); written by make_strict_targets.py",
-             "# 'volume seed n_labels crc32' then 'seed label target' for every finite target"]
-    body = []
-    for seed in BENCH_SEEDS:
+    lines = ["# strict sphericity targets (FP64 oracle, Eq. 1 on marching-tetrahedra meshes) of",
+             f"# synth.training_particles({BENCH_EDGE}, seed); written by make_strict_targets.py",
+             f"# train: the first {BENCH_TRAIN} volumes; held out: the rest",
+             "# 'volume seed n_labels crc32', then 'smooth seed t_1 .. t_{n-1}' (smoothed indicator, mesh volume)",
+             "# and 'binary seed t_1 .. t_{n-1}' (binary indicator, voxel count); nan: no voxel or no surface"]
+    for seed in range(BENCH_SEED0, BENCH_SEED0 + BENCH_VOLUMES):
         _, lab, n = synth.training_particles(BENCH_EDGE, seed)
-        T = targets(lab, n)
         lines.append(f"volume {seed} {n} {crc(lab)}")
-        body += [f"{seed} {l} {T[l]:.17g}" for l in range(1, n) if np.isfinite(T[l])]
+        lines.append(f"smooth {seed} " + _fmt(targets(lab, n)))
+        lines.append(f"binary {seed} " + _fmt(L.strict_sphericity_binary(lab, n)))
+        print(f"volume {seed}: {n - 1} labels", file=sys.stderr, flush=True)
     with open(BENCH_FILE, "w") as f:
-        f.write("\n".join(lines + body) + "\n")
+        f.write("\n".join(lines) + "\n")
 
 
 def read_bench(path: str = BENCH_FILE):
-    """{seed: (n_labels, crc32, targets[n_labels] with NaN where absent)}"""
-    vols, rows = {}, []
+    """{seed: (n_labels, crc32, smoothed targets, binary targets)}, targets
+    as float64 arrays of n_labels with NaN where absent (label 0 NaN)."""
+    out = {}
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
             p = line.split()
+            seed = int(p[1])
             if p[0] == "volume":
-                vols[int(p[1])] = (int(p[2]), int(p[3]))
+                out[seed] = [int(p[2]), int(p[3]), None, None]
             else:
-                rows.append((int(p[0]), int(p[1]), float(p[2])))
-    out = {}
-    for seed, (n, c) in vols.items():
-        T = np.full(n, np.nan)
-        out[seed] = (n, c, T)
-    for seed, l, t in rows:
-        out[seed][2][l] = t
-    return out
+                T = np.full(out[seed][0], np.nan)
+                T[1:] = np.array([float(v) for v in p[2:]], np.float64)
+                out[seed][2 if p[0] == "smooth" else 3] = T
+    return {k: tuple(v) for k, v in out.items()}
 
 
 def write_c4(path: str, n_train: int, edge: int, threads: int) -> None:

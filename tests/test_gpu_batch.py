@@ -36,13 +36,28 @@ def make_item(mask, labels, n):
             "n_labels": n}
 
 
+def _blobs(shape, seed):
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(seed)
+    f = ndi.gaussian_filter(rng.random(shape), 1.5)
+    m = (f > np.quantile(f, 0.6)).astype(np.uint8)
+    lab = ndi.label(m)[0].astype(np.uint32)
+    return m, lab, int(lab.max()) + 1
+
+
 def volumes():
+    """3D volumes of several sizes (rows of a multiple of 4 voxels and not,
+    TMA and plain-load ridge passes), 2D images (one with columns longer than
+    the shared-memory tiles: the global-memory y pass), and a 3D volume with
+    an axis over 2048 (run as a single chain inside the graph)."""
     out = []
     for seed, edge in enumerate((40, 64, 33, 96, 72)):
         out.append(synth.workload(f"particles_3d_{edge}", seed))
     out.append(synth.workload("ellipses_2d_256", 3))
     out.append(synth.workload("ellipses_2d_300", 4))
     out.append(synth.workload("ellipsoids_3d_128", 5))
+    out.append(synth.packed((2100, 90), 180, 8.0, 18.0, 6, shrink=(0.72, 0.86))[:2] + (181,))
+    out.append(_blobs((2050, 6, 9), 7))
     return out
 
 

@@ -235,3 +235,26 @@ def test_inference_bounds_hold_float32_evaluations(seed):
     inside = (yb[ok] >= lo[ok]) & (yb[ok] <= hi[ok])
     clamped = (yb[ok] == 0) | (yb[ok] == 1)
     assert np.count_nonzero(~inside & ~clamped) > 0.8 * np.count_nonzero(~clamped)
+
+
+def test_binary_strict_sphericity_of_cubes_and_balls():
+    """Binary-indicator target: the mesh of an n-cube is a quadratic in n with
+    leading term 6 n^2 (pinned above), so with V = n^3 voxels the value tends
+    to the cube's sphericity (pi/6)^(1/3) = 0.806 with an O(1/n) error. For
+    digital balls the staircase surface is a fixed fraction larger than the
+    sphere's whatever the radius, so the value settles near 0.79 instead of
+    approaching 1."""
+    lim = (math.pi / 6.0) ** (1.0 / 3.0)
+    errs = []
+    for n in (8, 16, 32):
+        s = L.strict_sphericity_binary(_cube(n), 2)[1]
+        errs.append(abs(s - lim))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.01
+    assert errs[1] / errs[2] == pytest.approx(2.0, rel=0.2)  # first order in 1/n
+    vals = []
+    for r in (8, 16):
+        n = 2 * r + 9
+        g = np.indices((n, n, n)) - n // 2
+        ball = ((g ** 2).sum(0) <= r * r).astype(np.uint32)
+        vals.append(L.strict_sphericity_binary(ball, 2)[1])
+    assert all(0.75 < v < 0.85 for v in vals) and abs(vals[0] - vals[1]) < 0.01
