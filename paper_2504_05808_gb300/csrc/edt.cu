@@ -45,12 +45,38 @@ __device__ __forceinline__ uint32_t zero_bits(const uint8_t* __restrict__ row, i
   return bits;
 }
 
+// Rows whose length is not a multiple of 16 start at any byte: a warp copies
+// its 512-voxel segment of the mask into shared memory with coalesced byte
+// loads (voxels past the row read as foreground) and each lane takes its 16
+// bytes from there as one aligned vector.
+__device__ __forceinline__ uint32_t zero_bits_staged(const uint8_t* __restrict__ row, int seg0, int nx,
+                                                     uint8_t* buf) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+#pragma unroll 4
+  for (int k = lane; k < kSeg; k += 32) buf[k] = seg0 + k < nx ? row[seg0 + k] : (uint8_t)1;
+  __syncwarp();
+  const uint4 q = *reinterpret_cast<const uint4*>(buf + lane * 16);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t bits = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t m = __vcmpeq4(w[k], 0u) & 0x01010101u;
+    bits |= ((m & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << (4 * k);
+  }
+  return bits;
+}
+
 // One warp per row (8 rows per CTA, block rb). Output: g per voxel (0 on
-// background), 16 bits.
+// background), 16 bits. VEC: rows of a multiple of 16 voxels, read and
+// written with 16-byte vectors; otherwise through a per-warp staging buffer
+// in shared memory with coalesced scalar accesses.
 template <bool VEC>
 __device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, uint16_t* __restrict__ out,
                                               int nx, uint32_t nrows, uint32_t rb) {
-  const int lane = threadIdx.x & 31;
+  __shared__ __align__(16) uint8_t stage_m[VEC ? 1 : 8][VEC ? 16 : kSeg];
+  __shared__ __align__(16) uint16_t stage_g[VEC ? 1 : 8][VEC ? 8 : kSeg];
+  const int lane = threadIdx.x & 31, wid = VEC ? 0 : (int)(threadIdx.x >> 5);
   const uint32_t row = rb * 8u + (threadIdx.x >> 5);
   if (row >= nrows) return;  // uniform per warp
   const uint8_t* mrow = mask + (size_t)row * nx;
@@ -61,7 +87,7 @@ __device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, 
   int segfirst = kBig;
   for (int s = 0; s < nseg; ++s) {
     const int x0 = s * kSeg + lane * 16;
-    const uint32_t z = zero_bits<VEC>(mrow, x0, nx);
+    const uint32_t z = VEC ? zero_bits<true>(mrow, x0, nx) : zero_bits_staged(mrow, s * kSeg, nx, stage_m[wid]);
     int f = z ? x0 + __ffs(z) - 1 : kBig;
 #pragma unroll
     for (int o = 16; o; o >>= 1) f = min(f, __shfl_xor_sync(kFull, f, o));
@@ -81,7 +107,7 @@ __device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, 
     int after = __shfl_sync(kFull, suf, (s + 1) & 31);
     if (s + 1 >= nseg) after = kBig;
     after = min(after, nx);  // virtual background at nx
-    const uint32_t z = zero_bits<VEC>(mrow, x0, nx);
+    const uint32_t z = VEC ? zero_bits<true>(mrow, x0, nx) : zero_bits_staged(mrow, s * kSeg, nx, stage_m[wid]);
     const int lastz = z ? x0 + 31 - __clz(z) : -1;
     const int firstz = z ? x0 + __ffs(z) - 1 : kBig;
     int incl = lastz;  // inclusive prefix max over lanes
@@ -119,16 +145,27 @@ __device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, 
       const int x = x0 + j;
       g[j] = (uint32_t)min(x - lpos[j], R - x);
     }
+    const uint4 o0 = make_uint4(g[0] | (g[1] << 16), g[2] | (g[3] << 16), g[4] | (g[5] << 16), g[6] | (g[7] << 16));
+    const uint4 o1 =
+        make_uint4(g[8] | (g[9] << 16), g[10] | (g[11] << 16), g[12] | (g[13] << 16), g[14] | (g[15] << 16));
     if (VEC && x0 + 16 <= nx) {
       uint4* o4 = reinterpret_cast<uint4*>(orow + x0);
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-        o4[k] = make_uint4(g[8 * k] | (g[8 * k + 1] << 16), g[8 * k + 2] | (g[8 * k + 3] << 16),
-                           g[8 * k + 4] | (g[8 * k + 5] << 16), g[8 * k + 6] | (g[8 * k + 7] << 16));
-    } else {
+      o4[0] = o0;
+      o4[1] = o1;
+    } else if (VEC) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         if (x0 + j < nx) orow[x0 + j] = (uint16_t)g[j];
+    } else {  // through the staging buffer, then coalesced 2-byte stores
+      uint16_t* sg = stage_g[wid];
+      reinterpret_cast<uint4*>(sg + lane * 16)[0] = o0;
+      reinterpret_cast<uint4*>(sg + lane * 16)[1] = o1;
+      __syncwarp();
+      const int sx = s * kSeg;
+#pragma unroll 4
+      for (int k = lane; k < kSeg; k += 32)
+        if (sx + k < nx) orow[sx + k] = sg[k];
+      __syncwarp();
     }
   }
 }

@@ -169,34 +169,56 @@ __global__ void __launch_bounds__(256) features_hist4_kernel(const uint32_t* __r
   if (key != 0xffffffffu && (lane == 31 || knext != key)) atomicAdd(hist + key, cnt);
 }
 
-__global__ void features_final_kernel(uint32_t n_labels, lt_object_stats st, const float* __restrict__ S,
-                                      const float* __restrict__ R, const uint32_t* __restrict__ hist,
-                                      float* __restrict__ F) {
-  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= n_labels) return;
-  float* f = F + (size_t)l * kF;
+// One thread per (label, feature index), so that consecutive threads write
+// consecutive floats of the [n_labels][48] matrix.
+__global__ void __launch_bounds__(256) features_final_kernel(uint32_t n_labels, lt_object_stats st,
+                                                             const float* __restrict__ S,
+                                                             const float* __restrict__ R,
+                                                             const uint32_t* __restrict__ hist,
+                                                             float* __restrict__ F) {
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (size_t)n_labels * kF) return;
+  const uint32_t l = (uint32_t)(g / kF);
+  const int i = (int)(g % kF);
   const uint32_t V = l ? st.volume[l] : 0u;
-  if (V == 0) {
-    for (int i = 0; i < kF; ++i) f[i] = 0.0f;
-    return;
+  float f = 0.0f;
+  if (V != 0 && i < 38) {
+    const uint32_t ns = st.n_shell[l];
+    if (i == 0) {
+      f = (float)(log((double)V) / 10.0);
+    } else if (i == 1) {
+      f = (float)(log((double)ns) / 10.0);
+    } else if (i == 2) {
+      f = (float)(log(sqrt((double)st.max_lt2[l])) / 4.0);
+    } else if (i == 3) {
+      const double mean = (double)st.sum_lt[l] / 1048576.0 / (double)V;
+      f = (float)(mean / sqrt((double)st.max_lt2[l]));
+    } else if (i == 4) {
+      f = R[l];
+    } else if (i == 5) {
+      f = S[l];
+    } else if (i < 22) {
+      f = (float)((double)hist[(size_t)l * 32 + (i - 6)] / (double)max(1u, V - ns));
+    } else {
+      f = (float)((double)hist[(size_t)l * 32 + 16 + (i - 22)] / (double)max(1u, ns));
+    }
   }
-  const uint32_t ns = st.n_shell[l];
-  const double M = sqrt((double)st.max_lt2[l]);
-  const double mean = (double)st.sum_lt[l] / 1048576.0 / (double)V;
-  f[0] = (float)(log((double)V) / 10.0);
-  f[1] = (float)(log((double)ns) / 10.0);
-  f[2] = (float)(log(M) / 4.0);
-  f[3] = (float)(mean / M);
-  f[4] = R[l];
-  f[5] = S[l];
-  const uint32_t* h = hist + (size_t)l * 32;
-  const double ni = (double)max(1u, V - ns), nsd = (double)max(1u, ns);
-  for (int b = 0; b < 16; ++b) {
-    f[6 + b] = (float)((double)h[b] / ni);
-    f[22 + b] = (float)((double)h[16 + b] / nsd);
-  }
-  for (int i = 38; i < kF; ++i) f[i] = 0.0f;
+  F[g] = f;
 }
+
+}  // namespace
+
+cudaError_t features_final_launch(uint32_t n_labels, const lt_object_stats& st, const float* S, const float* R,
+                                  const uint32_t* hist, float* F, cudaStream_t s) {
+  const size_t n = (size_t)n_labels * kF;
+  {
+    TraceScope t("features_final", s);
+    features_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_labels, st, S, R, hist, F);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
 
 // --------------------------------------------------------------- network
 // BF16-rounded weights staged in shared memory as floats.
@@ -386,11 +408,7 @@ cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_
   cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)n_labels * 32 * 4, s);
   if (e == cudaSuccess) e = features_hist_launch(labels, lt2, n_labels, d, st.max_lt2, hist, s);
   if (e != cudaSuccess) return e;
-  {
-    TraceScope t("features_final", s);
-    features_final_kernel<<<(n_labels + 255) / 256, 256, 0, s>>>(n_labels, st, S, R, hist, F);
-  }
-  return cudaGetLastError();
+  return features_final_launch(n_labels, st, S, R, hist, F, s);
 }
 
 cudaError_t mlp_infer_launch(const float* params, const float* F, const float* S, uint32_t n, float* out,

@@ -452,20 +452,19 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
     tma_load_3d(sD[s], map_dt2, x0 - kOX, y0 - 1, p, &bar[s]);
     tma_load_3d(sL[s], map_lab, x0 - kOX, y0 - 1, p, &bar[s]);
   };
+  // without TMA: asynchronous 4-byte copies of the halo plane (zeros outside
+  // the array), one commit group per plane
   auto load_plane = [&](int z) {
     const int s = slot_of(z);
     for (int i = tid; i < (kTX + 2) * kBY; i += 256) {
       const int hx = i % (kTX + 2), hy = i / (kTX + 2);
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      uint32_t dv = 0u, lv = 0u;
-      if (z >= 0 && z < d.nz && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny) {
-        const size_t g = (size_t)z * plane + (size_t)gy * d.nx + gx;
-        dv = dt2[g];
-        lv = labels[g];
-      }
-      sD[s][hy * kBX + hx + kOX - 1] = dv;
-      sL[s][hy * kBX + hx + kOX - 1] = lv;
+      const bool in = z >= 0 && z < d.nz && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+      const size_t g = in ? (size_t)z * plane + (size_t)gy * d.nx + gx : 0;
+      cp_async4(&sD[s][hy * kBX + hx + kOX - 1], dt2 + g, in);
+      cp_async4(&sL[s][hy * kBX + hx + kOX - 1], labels + g, in);
     }
+    cp_async_commit();
   };
   // appends records to the shared buffer: list A from its front, list B
   // from its back (all lanes of the warp call it)
@@ -503,6 +502,7 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
       for (int p = z0 - 1; p <= min(z1, z0 + 1); ++p) issue(p);
   } else {
     load_plane(z0 - 1);
+    load_plane(z0);
   }
   bool touch = false;  // this thread saw two face-adjacent foreground voxels with different labels
   for (int z = z0; z <= z1 + 1; ++z) {
@@ -513,8 +513,14 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
         if (z == z0) ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1), wt.limit_ns);
         ok = ok && mbar_wait(&bar[slot_of(z)], parity_of(z), wt.limit_ns);
       } else {
-        load_plane(z);    // (outside the array: zeros)
-        __syncthreads();  // plain loads of other threads
+        // plane z + 1 (into the slot plane z - 3 left in the last iteration)
+        // flies while this plane is worked on; plane z has landed once at
+        // most the newest group is pending, and the barrier shows every
+        // thread's copies
+        if (z + 1 <= z1) load_plane(z + 1);
+        else cp_async_commit();
+        cp_async_wait_but_one();
+        __syncthreads();
       }
     }
     // stage 1, every voxel of plane z: clear LT2, label check, compaction.

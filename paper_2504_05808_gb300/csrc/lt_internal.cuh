@@ -199,6 +199,10 @@ cudaError_t measure_features_launch(const uint8_t* mask, const uint32_t* labels,
 // histogram pass of the features (a separate pass over labels and LT2)
 cudaError_t features_hist_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                                  const uint32_t* max_lt2, uint32_t* hist, cudaStream_t s);
+// the [n_labels][48] feature matrix from the per-object sums (volume,
+// n_shell, max_lt2, sum_lt of st), S, R and the histograms hist[n][32]
+cudaError_t features_final_launch(uint32_t n_labels, const lt_object_stats& st, const float* S, const float* R,
+                                  const uint32_t* hist, float* F, cudaStream_t s);
 size_t features_workspace_bytes(uint32_t n_labels);
 cudaError_t features_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                             const lt_object_stats& st, const float* S, const float* R, void* body, float* F,

@@ -369,6 +369,116 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
                                          make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
 }
 
+// z-marching form for 3D volumes with nx % 4 == 0: a thread owns 4
+// consecutive voxels of one row (x0 .. x0+3, y) and walks kZChunk planes of
+// z; the labels of the planes below and above stay in registers (the z
+// neighbours of the shell test), and the sums of the thread's current object
+// accumulate in registers until the object changes, when they go out as one
+// set of atomics (a column meets a new object every ~2R planes, so this is
+// far fewer atomics than one per warp and plane). A voxel of a second object
+// within the same four voxels flushes and switches too (touching objects).
+// With HIST the thread also counts its current object's voxels per (shell,
+// LT/M bin) in shared memory (counter b of thread t at b * 256 + t, so the
+// threads of a warp hit distinct banks), flushed with the sums.
+constexpr int kZChunk = 32;
+
+template <bool HIST>
+__device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__ labels,
+                                                    const uint32_t* __restrict__ lt2, const Dims& d,
+                                                    uint32_t n_labels, const ShapeAcc& acc,
+                                                    WsHeader* __restrict__ hdr, int z_lo, int z_hi,
+                                                    const uint32_t* __restrict__ ref_max,
+                                                    uint32_t* __restrict__ hist, uint32_t* __restrict__ hs,
+                                                    uint3 blk) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int x0 = 4 * ((int)blk.x * blockDim.x + threadIdx.x);
+  const int y = (int)blk.y * blockDim.y + threadIdx.y;
+  const int zb = z_lo + (int)blk.z * kZChunk, ze = min(z_hi, zb + kZChunk);
+  if (x0 >= d.nx || y >= d.ny || zb >= ze) return;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const uint32_t* col = labels + (size_t)y * sy + x0;  // this thread's labels at z = 0
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  auto lab4 = [&](int z) { return *reinterpret_cast<const uint4*>(col + (size_t)z * sz); };
+  uint4 Lm = zb > 0 ? lab4(zb - 1) : zero, L = lab4(zb);
+  uint32_t cl = 0, mref = 0, cnt = 0, shc = 0, mx = 0;
+  unsigned long long q = 0, qs = 0;
+  bool bad = false;
+  auto flush = [&]() {
+    if (cl == 0) return;
+    atomicAdd(acc.volume + cl, cnt);
+    if (shc) atomicAdd(acc.n_shell + cl, shc);
+    atomicAdd(acc.sum_lt + cl, q);
+    if (shc) atomicAdd(acc.sum_shell_lt + cl, qs);
+    atomicMax(acc.max_lt2 + cl, mx);
+    if (HIST)
+      for (int b = 0; b < 32; ++b) {
+        const uint32_t c = hs[b * 256 + tid];
+        if (c) {
+          atomicAdd(hist + cl * 32u + b, c);
+          hs[b * 256 + tid] = 0u;
+        }
+      }
+    cnt = shc = mx = 0;
+    q = qs = 0;
+  };
+  for (int z = zb; z < ze; ++z) {
+    const uint4 Lp = z + 1 < d.nz ? lab4(z + 1) : zero;
+    if ((L.x | L.y | L.z | L.w) != 0u) {
+      const size_t v = (size_t)z * sz + (size_t)y * sy + x0;
+      const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
+      const uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
+      const uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
+      const uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
+      const uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t l = comp(L, k);
+        if (l == 0) continue;
+        if (l >= n_labels) {
+          bad = true;
+          continue;
+        }
+        const uint32_t left = k == 0 ? xl : comp(L, k - 1), right = k == 3 ? xr : comp(L, k + 1);
+        const bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l || comp(Lm, k) != l ||
+                       comp(Lp, k) != l;
+        const uint32_t t = comp(T, k);
+        const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
+        if (l != cl) {
+          flush();
+          cl = l;
+          if (HIST) mref = ref_max[l];
+        }
+        ++cnt;
+        shc += s ? 1u : 0u;
+        mx = max(mx, t);
+        q += qq;
+        qs += s ? qq : 0ull;
+        if (HIST) ++hs[((s ? 16u : 0u) + lt_bin16(t, mref)) * 256 + tid];
+      }
+    }
+    Lm = L;
+    L = Lp;
+  }
+  flush();
+  if (bad) atomicOr(&hdr->error, ERR_LABEL_RANGE);
+}
+
+template <bool HIST>
+__global__ void __launch_bounds__(256) shape_reduce_z_kernel(const uint32_t* __restrict__ labels,
+                                                             const uint32_t* __restrict__ lt2, Dims d,
+                                                             uint32_t n_labels, ShapeAcc acc,
+                                                             WsHeader* __restrict__ hdr, int z_lo, int z_hi,
+                                                             const uint32_t* __restrict__ ref_max,
+                                                             uint32_t* __restrict__ hist) {
+  __shared__ uint32_t hs[HIST ? 32 * 256 : 1];
+  if (HIST) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int b = 0; b < 32; ++b) hs[b * 256 + tid] = 0u;  // each thread clears its own counters
+  }
+  shape_reduce_z_body<HIST>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, ref_max, hist, hs,
+                            make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+}
+
 // The shape reduction over many volumes (each volume's accumulators at the
 // start of its workspace body): VEC4 with the 64 x 4 blocks of the vector
 // form (rows of a multiple of 4 voxels), else the one-voxel form.
@@ -377,7 +487,10 @@ __global__ void __launch_bounds__(256) shape_reduce_multi_kernel(MultiArgs m) {
   uint3 blk;
   const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
   const ShapeAcc acc = acc_layout(p.body, p.n_labels);
-  if (VEC4)
+  if (VEC4 && NDIM == 3)
+    shape_reduce_z_body<false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0, p.d.nz, nullptr, nullptr, nullptr,
+                               blk);
+  else if (VEC4)
     shape_reduce4_body<NDIM, false, false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0u, 0, nullptr, nullptr,
                                            blk);
   else
@@ -429,28 +542,7 @@ __device__ __forceinline__ void shape_finalize_body(const ShapeAcc& acc, uint32_
   }
   if (S) S[l] = (float)sph;
   if (R) R[l] = (float)rnd;
-  if (F) {
-    // the learned correction's features of the object (zero for empty
-    // labels): 0 log(V)/10, 1 log(n_shell)/10, 2 log(M)/4, 3 (mean LT)/M,
-    // 4 R, 5 S, 6-21 interior and 22-37 shell fractions per LT/M bin, 38-47 0
-    float* f = F + (size_t)l * LT_MLP_FEATURES;
-    for (int i = 0; i < LT_MLP_FEATURES; ++i) f[i] = 0.0f;
-    if (V > 0) {
-      const double M = sqrt((double)mx);
-      f[0] = (float)(log((double)V) / 10.0);
-      f[1] = (float)(log((double)ns) / 10.0);
-      f[2] = (float)(log(M) / 4.0);
-      f[3] = (float)((double)sl / 1048576.0 / (double)V / M);
-      f[4] = (float)rnd;
-      f[5] = (float)sph;
-      const uint32_t* h = hist + (size_t)l * 32;
-      const double ni = (double)max(1u, V - ns), nsd = (double)max(1u, ns);
-      for (int b = 0; b < 16; ++b) {
-        f[6 + b] = (float)((double)h[b] / ni);
-        f[22 + b] = (float)((double)h[16 + b] / nsd);
-      }
-    }
-  }
+
 }
 
 template <int NDIM>
@@ -532,7 +624,12 @@ template <int NDIM, bool FILTER>
 void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                    const ShapeAcc& acc, WsHeader* hdr, uint32_t min_lt2, int z_lo, int z_hi, cudaStream_t s) {
   TraceScope t("shape_reduce", s);
-  if (d.nx % 4 == 0) {
+  if (NDIM == 3 && !FILTER && d.nx % 4 == 0) {
+    // 64 x 4 threads (256 x 4 voxels of a plane), kZChunk planes each
+    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, (z_hi - z_lo + kZChunk - 1) / kZChunk);
+    shape_reduce_z_kernel<false>
+        <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, nullptr, nullptr);
+  } else if (d.nx % 4 == 0) {
     // 64 threads (256 voxels) per row, 4 rows per CTA
     dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, z_hi - z_lo);
     shape_reduce4_kernel<NDIM, FILTER, false>
@@ -595,7 +692,8 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
 // clear accumulators.
 dim3 shape_multi_grid(const Dims& d, uint32_t n_labels, int kind) {
   switch (kind) {
-    case 0: return dim3((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    case 0:
+      return dim3((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.ndim == 3 ? (d.nz + kZChunk - 1) / kZChunk : d.nz);
     case 1: return dim3((d.nx + 255) / 256, d.ny, d.nz);
     case 2: return dim3((n_labels + 255) / 256, 1, 1);
     case 3: return dim3(1, 1, 1);
@@ -642,30 +740,25 @@ cudaError_t shape_features_launch(const uint32_t* labels, const uint32_t* lt2, u
   if (e != cudaSuccess) return e;
   if (d.nx % 4 == 0) {
     TraceScope t("shape_reduce_features", s);
-    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
-    if (d.ndim == 3)
-      shape_reduce4_kernel<3, false, true>
-          <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0u, 0, ref_max, hist);
-    else
+    if (d.ndim == 3) {
+      dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, (d.nz + kZChunk - 1) / kZChunk);
+      shape_reduce_z_kernel<true><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0, d.nz, ref_max, hist);
+    } else {
+      dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
       shape_reduce4_kernel<2, false, true>
           <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0u, 0, ref_max, hist);
+    }
     e = cudaGetLastError();
   } else {  // rows not a multiple of 4 voxels: the histograms in a pass of their own
     e = shape_accumulate(labels, lt2, n_labels, d, hdr, body, 0, d.nz, s, 0u);
     if (e == cudaSuccess) e = features_hist_launch(labels, lt2, n_labels, d, ref_max, hist, s);
   }
   if (e != cudaSuccess) return e;
-  lt_object_stats st = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (stats) st = *stats;
-  const unsigned blocks = (n_labels + 255) / 256;
-  {
-    TraceScope t("shape_finalize_features", s);
-    if (d.ndim == 3)
-      shape_finalize_kernel<3><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, hist, F);
-    else
-      shape_finalize_kernel<2><<<blocks, 256, 0, s>>>(acc, n_labels, S, R, st, hist, F);
-  }
-  return cudaGetLastError();
+  e = shape_finalize(d.ndim, n_labels, body, S, R, stats, s);
+  if (e != cudaSuccess) return e;
+  const lt_object_stats sums = {acc.volume, acc.n_shell, acc.max_lt2, reinterpret_cast<uint64_t*>(acc.sum_lt),
+                                reinterpret_cast<uint64_t*>(acc.sum_shell_lt)};
+  return features_final_launch(n_labels, sums, S, R, hist, F, s);
 }
 
 }  // namespace ltk
