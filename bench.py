@@ -383,7 +383,7 @@ def learned_eval(lt, args, dev, mask, labels, n_labels):
         "plain_finalize_ns_per_object": tr.get("shape_finalize", 0.0) * 1e6 / objs,
         "plain_ns_per_object": t_plain * 1e6 / objs,
         "shape_reduce_ms": tr.get("shape_reduce"), "shape_reduce_features_ms": tr.get("shape_reduce_features"),
-        "finalize_features_ms": tr.get("shape_finalize_features")}
+        "features_final_ms": tr.get("features_final")}
     return res
 
 

@@ -68,13 +68,13 @@ constexpr uint32_t kNoDominant = 31u;
 constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a crescent table
 constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
 constexpr int kChunkR2D = 64;   // 2D: largest r^2 painted in shared chunks (bigger discs: a warp each)
-constexpr uint32_t kParts = 4;          // warps sharing one big row-mode centre, at most
-constexpr uint32_t kStepsPerPart = 12;  // row steps (32 rows each) per sharing warp, at least
+constexpr uint32_t kParts = 4096;      // warps sharing one big row-mode centre, at most
+constexpr uint32_t kStepsPerPart = 2;  // row steps (32 rows each) per sharing warp, at least
 
 // Centre records: at most one per voxel, plus the extra part records of the
 // shared row-mode centres (at most n/8). The front list starts at 0, the
 // back list at the last slot.
-__host__ __device__ __forceinline__ size_t record_capacity(uint32_t n) { return (size_t)n + n / 8 + kParts; }
+__host__ __device__ __forceinline__ size_t record_capacity(uint32_t n) { return (size_t)n + n / 8 + 4; }
 constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
@@ -272,7 +272,7 @@ __device__ __forceinline__ uint32_t cres_combo(const uint16_t* base, int cls, ui
 //   crescent size << 16.
 //   Painting needs no other lookup.
 //   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
-//   z = the two extra codes; w = part | parts << 8 (row-mode centres go to
+//   z = the two extra codes; w = part | parts << 16 (row-mode centres go to
 //   the back list directly; a big one as up to kParts records, one per
 //   part, while the extra records stay within n/8).
 constexpr int kTX = 64, kTY = 8;
@@ -381,8 +381,9 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
   keepB = !keepA;
   if (keepB && (NDIM == 2 || !tab)) {
     // painted row by row, written at once (these centres are rare): a big
-    // ball as kParts records, one per warp sharing it (w = part | parts <<
-    // 8), while the extra records fit their budget of n/8
+    // ball as up to kParts records, one per warp sharing it (w = part | parts <<
+    // 16; about 2 row steps of 32 rows per part), while the extra records fit
+    // their budget of n/8
     keepB = false;
     const int side = 2 * (int)isqrt24(r2) + 1;
     const uint32_t steps = (uint32_t)((NDIM == 3 ? side * side : side) + 31) / 32;  // row steps
@@ -390,7 +391,7 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
     if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
     const uint32_t bb = atomicAdd(&hdr->n_big, parts);
     for (uint32_t q = 0; q < parts; ++q)
-      surv[record_capacity(d.n) - 1 - (bb + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 8));
+      surv[record_capacity(d.n) - 1 - (bb + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 16));
   }
   return rec;
 }
@@ -409,6 +410,10 @@ struct RidgeSmem {
   // list counts by plane mod 3: filled in one iteration, read in the next,
   // cleared in the one after
   uint32_t nwork_s[3], nkept_s[3];
+  // records each warp appended since the last flush, published before the
+  // barrier of plane z in slot z & 1 (untouched until the next barrier), so
+  // that every thread reads the same total after it
+  uint32_t wrec[2][8];
   uint16_t sbase[NDIM == 3 ? 3 * (kCresT + 1) : 2];  // copy of g_cres_base
 };
 
@@ -433,6 +438,7 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
   auto& flags = sm.flags;
   auto& nwork_s = sm.nwork_s;
   auto& nkept_s = sm.nkept_s;
+  auto& wrec = sm.wrec;
   auto& sbase = sm.sbase;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = (int)blk.x * kTX, y0 = (int)blk.y * kTY;
@@ -468,8 +474,10 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
   };
   // appends records to the shared buffer: list A from its front, list B
   // from its back (all lanes of the warp call it)
+  uint32_t appended = 0;  // records this warp appended since the last flush
   auto append = [&](bool keepA, bool keepB, const uint4& rec) {
     const unsigned ba = __ballot_sync(kFull, keepA), bb = __ballot_sync(kFull, keepB);
+    appended += (uint32_t)(__popc(ba) + __popc(bb));
     if (ba) {
       uint32_t wb = 0;
       if (lane == 0) wb = atomicAdd(&cntA, (uint32_t)__popc(ba));
@@ -652,6 +660,7 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
       nwork_s[(z + 1) % 3] = 0;  // plane z - 2's count: read in iteration z - 1, refilled in z + 1
       nkept_s[z % 3] = 0;        // plane z - 3's count: read in iteration z - 1, refilled in z + 1
     }
+    if (lane == 0) wrec[z & 1][warp] = appended;
     // the one barrier of the plane; it also agrees on a timed-out wait
     if (__syncthreads_or(!ok)) {
       // record the timeout, wait (again bounded) for the copies this CTA
@@ -667,15 +676,23 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
       fence_proxy_async();
       issue(z + 2);
     }
-    if (cntA + cntB > kListBuf - kTile || z == z1 + 1) {  // uniform: read after the barrier
+    // buffered records: the same sum for every thread (fast warps already
+    // append the next plane's records, to cntA/cntB and to the other slot)
+    uint32_t held = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) held += wrec[z & 1][w];
+    if (held > (uint32_t)(kListBuf - kTile) || z == z1 + 1) {  // uniform
+      // nobody appends until the second barrier below: the counts are final
+      const uint32_t nA = cntA, nB = cntB;
       // the two list atomics from two warps, so that their latencies overlap
-      if (tid == 0) baseA = cntA ? atomicAdd(&hdr->n_surv, cntA) : 0u;
-      if (tid == 32) baseB = cntB ? atomicAdd(&hdr->n_big, cntB) : 0u;
-      __syncthreads();
-      for (uint32_t i = tid; i < cntA; i += 256) surv[baseA + i] = buf[i];
-      for (uint32_t i = tid; i < cntB; i += 256) surv[record_capacity(d.n) - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
+      if (tid == 0) baseA = nA ? atomicAdd(&hdr->n_surv, nA) : 0u;
+      if (tid == 32) baseB = nB ? atomicAdd(&hdr->n_big, nB) : 0u;
       __syncthreads();
       if (tid == 0) cntA = cntB = 0;
+      for (uint32_t i = tid; i < nA; i += 256) surv[baseA + i] = buf[i];
+      for (uint32_t i = tid; i < nB; i += 256) surv[record_capacity(d.n) - 1 - (baseB + i)] = buf[kListBuf - 1 - i];
+      appended = 0;
+      __syncthreads();
     }
   }
   if (__syncthreads_or(touch) && tid == 0) atomicOr(&hdr->touch, 1u);
@@ -1217,7 +1234,7 @@ __device__ __forceinline__ void paint_big(const uint4& rec, const Dims& d, size_
   } else {
     Centre c;
     make_centre<NDIM>(rec, d, sy, sz, touch, dt2, labels, c);
-    paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFu), max(1, (int)(rec.w >> 8)), d, sy, sz, touch, dt2, labels, lt2,
+    paint_centre_rows<NDIM>(c, (int)(rec.w & 0xFFFFu), max(1, (int)(rec.w >> 16)), d, sy, sz, touch, dt2, labels, lt2,
                             lut, nupd);
   }
 }

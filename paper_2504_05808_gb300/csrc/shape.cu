@@ -153,6 +153,17 @@ __device__ __forceinline__ uint32_t lt_bin16(uint32_t t, uint32_t mx) {
   return (uint32_t)b;
 }
 
+// The same bin with the object's 256 / mx precomputed (rmx): the float
+// estimate floor(sqrt(t * rmx)) is within one of b, and the two integer
+// checks are exact in 32 bits (b^2 <= 256, mx < 2^24, 256 t < 2^32).
+__device__ __forceinline__ uint32_t lt_bin16_r(uint32_t t, uint32_t mx, float rmx) {
+  uint32_t b = min(15u, (uint32_t)sqrtf((float)t * rmx));
+  const uint32_t T = 256u * t;
+  if (b < 15u && (b + 1) * (b + 1) * mx <= T) ++b;
+  if (b > 0u && b * b * mx > T) --b;
+  return b;
+}
+
 // Sums of one warp's 32 per-thread partials that all belong to one label
 // (or to none), by warp reductions: counts, max and the two fixed-point
 // sums (each split into 16-bit halves whose warp sums fit 32 bits: a
@@ -382,7 +393,15 @@ __global__ void __launch_bounds__(256) shape_reduce4_kernel(const uint32_t* __re
 // threads of a warp hit distinct banks), flushed with the sums.
 constexpr int kZChunk = 32;
 
-template <bool HIST>
+// Four consecutive uint32 at p (voxels x0 .. x0+3 of a row): one 16-byte load
+// when rows are 16-byte aligned (VEC), else scalar loads, zero past nx.
+template <bool VEC>
+__device__ __forceinline__ uint4 load_quad(const uint32_t* __restrict__ p, int x0, int nx) {
+  if (VEC) return *reinterpret_cast<const uint4*>(p);
+  return make_uint4(p[0], x0 + 1 < nx ? p[1] : 0u, x0 + 2 < nx ? p[2] : 0u, x0 + 3 < nx ? p[3] : 0u);
+}
+
+template <bool HIST, bool VEC>
 __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__ labels,
                                                     const uint32_t* __restrict__ lt2, const Dims& d,
                                                     uint32_t n_labels, const ShapeAcc& acc,
@@ -398,9 +417,10 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const uint32_t* col = labels + (size_t)y * sy + x0;  // this thread's labels at z = 0
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-  auto lab4 = [&](int z) { return *reinterpret_cast<const uint4*>(col + (size_t)z * sz); };
+  auto lab4 = [&](int z) { return load_quad<VEC>(col + (size_t)z * sz, x0, d.nx); };
   uint4 Lm = zb > 0 ? lab4(zb - 1) : zero, L = lab4(zb);
-  uint32_t cl = 0, mref = 0, cnt = 0, shc = 0, mx = 0;
+  uint32_t cl = 0, mref = 0, cnt = 0, shc = 0, mx = 0, used = 0;  // used: bins counted since the last flush
+  float rref = 0.f;
   unsigned long long q = 0, qs = 0;
   bool bad = false;
   auto flush = [&]() {
@@ -411,12 +431,11 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
     if (shc) atomicAdd(acc.sum_shell_lt + cl, qs);
     atomicMax(acc.max_lt2 + cl, mx);
     if (HIST)
-      for (int b = 0; b < 32; ++b) {
-        const uint32_t c = hs[b * 256 + tid];
-        if (c) {
-          atomicAdd(hist + cl * 32u + b, c);
-          hs[b * 256 + tid] = 0u;
-        }
+      while (used) {
+        const int b = __ffs(used) - 1;
+        used &= used - 1;
+        atomicAdd(hist + cl * 32u + b, hs[b * 256 + tid]);
+        hs[b * 256 + tid] = 0u;
       }
     cnt = shc = mx = 0;
     q = qs = 0;
@@ -425,9 +444,9 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
     const uint4 Lp = z + 1 < d.nz ? lab4(z + 1) : zero;
     if ((L.x | L.y | L.z | L.w) != 0u) {
       const size_t v = (size_t)z * sz + (size_t)y * sy + x0;
-      const uint4 T = *reinterpret_cast<const uint4*>(lt2 + v);
-      const uint4 Ym = y > 0 ? *reinterpret_cast<const uint4*>(labels + v - sy) : zero;
-      const uint4 Yp = y + 1 < d.ny ? *reinterpret_cast<const uint4*>(labels + v + sy) : zero;
+      const uint4 T = load_quad<VEC>(lt2 + v, x0, d.nx);
+      const uint4 Ym = y > 0 ? load_quad<VEC>(labels + v - sy, x0, d.nx) : zero;
+      const uint4 Yp = y + 1 < d.ny ? load_quad<VEC>(labels + v + sy, x0, d.nx) : zero;
       const uint32_t xl = x0 > 0 ? labels[v - 1] : 0u;
       const uint32_t xr = x0 + 4 < d.nx ? labels[v + 4] : 0u;
 #pragma unroll
@@ -446,14 +465,21 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
         if (l != cl) {
           flush();
           cl = l;
-          if (HIST) mref = ref_max[l];
+          if (HIST) {
+            mref = max(ref_max[l], 1u);
+            rref = 256.0f / (float)mref;
+          }
         }
         ++cnt;
         shc += s ? 1u : 0u;
         mx = max(mx, t);
         q += qq;
         qs += s ? qq : 0ull;
-        if (HIST) ++hs[((s ? 16u : 0u) + lt_bin16(t, mref)) * 256 + tid];
+        if (HIST) {
+          const uint32_t b = (s ? 16u : 0u) + lt_bin16_r(t, mref, rref);
+          atomicAdd(&hs[b * 256 + tid], 1u);  // the thread's own counter: no conflicts
+          used |= 1u << b;
+        }
       }
     }
     Lm = L;
@@ -463,7 +489,7 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
   if (bad) atomicOr(&hdr->error, ERR_LABEL_RANGE);
 }
 
-template <bool HIST>
+template <bool HIST, bool VEC>
 __global__ void __launch_bounds__(256) shape_reduce_z_kernel(const uint32_t* __restrict__ labels,
                                                              const uint32_t* __restrict__ lt2, Dims d,
                                                              uint32_t n_labels, ShapeAcc acc,
@@ -475,8 +501,13 @@ __global__ void __launch_bounds__(256) shape_reduce_z_kernel(const uint32_t* __r
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int b = 0; b < 32; ++b) hs[b * 256 + tid] = 0u;  // each thread clears its own counters
   }
-  shape_reduce_z_body<HIST>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, ref_max, hist, hs,
-                            make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+  shape_reduce_z_body<HIST, VEC>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, ref_max, hist, hs,
+                                 make_uint3(blockIdx.x, blockIdx.y, blockIdx.z));
+}
+
+// grid of the z-marching form over planes [z_lo, z_hi)
+inline dim3 z_grid(const Dims& d, int z_lo, int z_hi) {
+  return dim3(((d.nx + 3) / 4 + 63) / 64, (d.ny + 3) / 4, (z_hi - z_lo + kZChunk - 1) / kZChunk);
 }
 
 // The shape reduction over many volumes (each volume's accumulators at the
@@ -487,9 +518,9 @@ __global__ void __launch_bounds__(256) shape_reduce_multi_kernel(MultiArgs m) {
   uint3 blk;
   const VolParams& p = m.vols[find_volume(m, blockIdx.x, blk)];
   const ShapeAcc acc = acc_layout(p.body, p.n_labels);
-  if (VEC4 && NDIM == 3)
-    shape_reduce_z_body<false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0, p.d.nz, nullptr, nullptr, nullptr,
-                               blk);
+  if (NDIM == 3)
+    shape_reduce_z_body<false, VEC4>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0, p.d.nz, nullptr, nullptr,
+                                     nullptr, blk);
   else if (VEC4)
     shape_reduce4_body<NDIM, false, false>(p.labels, p.lt2, p.d, p.n_labels, acc, p.hdr, 0u, 0, nullptr, nullptr,
                                            blk);
@@ -624,11 +655,15 @@ template <int NDIM, bool FILTER>
 void launch_reduce(const uint32_t* labels, const uint32_t* lt2, uint32_t n_labels, const Dims& d,
                    const ShapeAcc& acc, WsHeader* hdr, uint32_t min_lt2, int z_lo, int z_hi, cudaStream_t s) {
   TraceScope t("shape_reduce", s);
-  if (NDIM == 3 && !FILTER && d.nx % 4 == 0) {
+  if (NDIM == 3 && !FILTER) {
     // 64 x 4 threads (256 x 4 voxels of a plane), kZChunk planes each
-    dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, (z_hi - z_lo + kZChunk - 1) / kZChunk);
-    shape_reduce_z_kernel<false>
-        <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, nullptr, nullptr);
+    const dim3 block(64, 4), grid = z_grid(d, z_lo, z_hi);
+    if (d.nx % 4 == 0)
+      shape_reduce_z_kernel<false, true>
+          <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, nullptr, nullptr);
+    else
+      shape_reduce_z_kernel<false, false>
+          <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, z_lo, z_hi, nullptr, nullptr);
   } else if (d.nx % 4 == 0) {
     // 64 threads (256 voxels) per row, 4 rows per CTA
     dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, z_hi - z_lo);
@@ -692,9 +727,8 @@ cudaError_t shape_launch(const uint32_t* labels, const uint32_t* lt2, uint32_t n
 // clear accumulators.
 dim3 shape_multi_grid(const Dims& d, uint32_t n_labels, int kind) {
   switch (kind) {
-    case 0:
-      return dim3((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.ndim == 3 ? (d.nz + kZChunk - 1) / kZChunk : d.nz);
-    case 1: return dim3((d.nx + 255) / 256, d.ny, d.nz);
+    case 0: return d.ndim == 3 ? z_grid(d, 0, d.nz) : dim3((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
+    case 1: return d.ndim == 3 ? z_grid(d, 0, d.nz) : dim3((d.nx + 255) / 256, d.ny, d.nz);
     case 2: return dim3((n_labels + 255) / 256, 1, 1);
     case 3: return dim3(1, 1, 1);
     default: return dim3((unsigned)((acc_bytes(n_labels) + 4095) / 4096), 1, 1);
@@ -712,7 +746,7 @@ cudaError_t shape_multi_launch(const MultiArgs& m, uint32_t blocks, int kind, in
   } else if (kind == 1) {
     TraceScope t("shape_reduce", s);
     if (ndim == 3)
-      shape_reduce_multi_kernel<3, false><<<blocks, 256, 0, s>>>(m);
+      shape_reduce_multi_kernel<3, false><<<blocks, dim3(64, 4), 0, s>>>(m);
     else
       shape_reduce_multi_kernel<2, false><<<blocks, 256, 0, s>>>(m);
   } else if (kind == 2) {
@@ -738,11 +772,16 @@ cudaError_t shape_features_launch(const uint32_t* labels, const uint32_t* lt2, u
   uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(body) + acc_bytes(n_labels));
   cudaError_t e = cudaMemsetAsync(body, 0, shape_features_bytes(n_labels), s);
   if (e != cudaSuccess) return e;
-  if (d.nx % 4 == 0) {
+  if (d.ndim == 3 || d.nx % 4 == 0) {
     TraceScope t("shape_reduce_features", s);
     if (d.ndim == 3) {
-      dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, (d.nz + kZChunk - 1) / kZChunk);
-      shape_reduce_z_kernel<true><<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0, d.nz, ref_max, hist);
+      const dim3 block(64, 4), grid = z_grid(d, 0, d.nz);
+      if (d.nx % 4 == 0)
+        shape_reduce_z_kernel<true, true>
+            <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0, d.nz, ref_max, hist);
+      else
+        shape_reduce_z_kernel<true, false>
+            <<<grid, block, 0, s>>>(labels, lt2, d, n_labels, acc, hdr, 0, d.nz, ref_max, hist);
     } else {
       dim3 block(64, 4), grid((d.nx / 4 + 63) / 64, (d.ny + 3) / 4, d.nz);
       shape_reduce4_kernel<2, false, true>
