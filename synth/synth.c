@@ -454,6 +454,117 @@ static int fits_cell(const vol_t* v, shape_t* sh, double s, const double c[3],
   return 1;
 }
 
+/* Does the particle (shape sh at scale s, centre c, label lab) fit where it
+ * stands: every voxel of its rasterisation off the volume faces and with no
+ * other label in its 26-neighbourhood (the one-voxel gap)? */
+static int grow_fits(const vol_t* v, shape_t* sh, double s, const double c[3], uint32_t lab) {
+  sh->s = s;
+  int64_t blo[3], bhi[3];
+  shape_box(v, sh, c, blo, bhi);
+  const int64_t n[3] = {v->nx, v->ny, v->nz};
+  const int nd = v->ndim;
+  for (int64_t z = blo[2]; z < bhi[2]; ++z)
+    for (int64_t y = blo[1]; y < bhi[1]; ++y)
+      for (int64_t x = blo[0]; x < bhi[0]; ++x) {
+        if (!inside_world(sh, c, (double)x, (double)y, (double)z)) continue;
+        const int64_t q[3] = {x, y, z};
+        for (int i = 0; i < nd; ++i)
+          if (q[i] < 1 || q[i] > n[i] - 2) return 0;
+        const int64_t z0 = nd == 3 ? z - 1 : z, z1 = nd == 3 ? z + 1 : z;
+        for (int64_t zz = z0; zz <= z1; ++zz)
+          for (int64_t yy = y - 1; yy <= y + 1; ++yy)
+            for (int64_t xx = x - 1; xx <= x + 1; ++xx) {
+              uint32_t o = v->labels[vidx(v, xx, yy, zz)];
+              if (o != 0u && o != lab) return 0;
+            }
+      }
+  return 1;
+}
+
+/* Voxel box of the particle at scale s widened by one voxel, unclamped. */
+static void grow_box(const shape_t* sh, double s, const double c[3], int ndim, int64_t lo[3],
+                     int64_t hi[3]) {
+  double ext[3];
+  world_extent(sh, s, ext);
+  for (int i = 0; i < 3; ++i) {
+    lo[i] = (int64_t)floor(c[i] - ext[i]) - 2;
+    hi[i] = (int64_t)ceil(c[i] + ext[i]) + 3;
+  }
+  if (ndim == 2) { lo[2] = 0; hi[2] = 1; }
+}
+
+/*
+ * Growth into free space, after the packing: each particle is scaled about
+ * its centre by the largest factor in [1, grow_max] (bisection, 8 steps) at
+ * which it still fits (grow_fits). The shapes are convex and contain their
+ * centre, so a grown particle covers its old voxels. Particles whose widened
+ * boxes at grow_max overlap never grow at the same time: a greedy colouring
+ * in label order splits them into rounds, and the particles of one round grow
+ * in parallel. The result depends on neither the thread count nor the
+ * schedule.
+ */
+static void grow_particles(vol_t* v, shape_t* shs, double (*cs)[3], const uint8_t* placed,
+                           int64_t ncells, double grow_max) {
+  int64_t (*box)[6] = (int64_t(*)[6])malloc(sizeof(int64_t[6]) * (size_t)ncells);
+  int32_t* colour = (int32_t*)malloc(sizeof(int32_t) * (size_t)ncells);
+  if (!box || !colour) { free(box); free(colour); return; }
+  int32_t ncol = 0;
+  for (int64_t i = 0; i < ncells; ++i) {
+    colour[i] = -1;
+    if (!placed[i]) continue;
+    grow_box(&shs[i], shs[i].s * grow_max, cs[i], v->ndim, &box[i][0], &box[i][3]);
+  }
+  uint64_t used[64];
+  for (int64_t i = 0; i < ncells; ++i) {
+    if (!placed[i]) continue;
+    memset(used, 0, sizeof(used));
+    for (int64_t j = 0; j < i; ++j) {
+      if (colour[j] < 0) continue;
+      int apart = 0;
+      for (int k = 0; k < 3; ++k)
+        if (box[i][k] >= box[j][k + 3] || box[j][k] >= box[i][k + 3]) { apart = 1; break; }
+      if (!apart && colour[j] < 4096) used[colour[j] >> 6] |= 1ull << (colour[j] & 63);
+    }
+    int32_t c = 0;
+    while (c < 4096 && (used[c >> 6] >> (c & 63) & 1ull)) ++c;
+    if (c >= 4096) continue; /* crowded beyond any real packing: leave it as placed */
+    colour[i] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  for (int32_t round = 0; round < ncol; ++round) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < ncells; ++i) {
+      if (colour[i] != round) continue;
+      shape_t sh = shs[i];
+      const uint32_t lab = (uint32_t)(i + 1);
+      const double s0 = sh.s;
+      double lo = 1.0, hi = grow_max;
+      if (grow_fits(v, &sh, s0 * hi, cs[i], lab)) {
+        lo = hi;
+      } else {
+        for (int it = 0; it < 8; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (grow_fits(v, &sh, s0 * mid, cs[i], lab)) lo = mid; else hi = mid;
+        }
+      }
+      if (lo <= 1.0) continue;
+      sh.s = s0 * lo;
+      int64_t blo[3], bhi[3];
+      shape_box(v, &sh, cs[i], blo, bhi);
+      for (int64_t z = blo[2]; z < bhi[2]; ++z)
+        for (int64_t y = blo[1]; y < bhi[1]; ++y)
+          for (int64_t x = blo[0]; x < bhi[0]; ++x)
+            if (inside_world(&sh, cs[i], (double)x, (double)y, (double)z)) {
+              int64_t q = vidx(v, x, y, z);
+              v->mask[q] = 1;
+              v->labels[q] = lab;
+            }
+    }
+  }
+  free(box);
+  free(colour);
+}
+
 /*
  * Dense packing of n_obj particles: the volume is split by weighted recursive
  * bisection into one cell per particle (cell volume proportional to a drawn
@@ -467,13 +578,14 @@ static int fits_cell(const vol_t* v, shape_t* sh, double s, const double c[3],
  * in [shrink_lo, shrink_hi] (1, 1 for the densest packing). Orientation: the
  * best of twelve candidates (uniform random rotations and tilted axis-aligned
  * ones in 3D, uniform in 2D). Cells are processed in parallel, each from its own PCG32 stream,
- * so the result does not depend on the thread count.
+ * so the result does not depend on the thread count. grow_max > 1 then
+ * grows every particle into the free space around it (grow_particles).
  * Returns the number of particles (labels 1..count; a particle too small to
  * hold a voxel leaves its label unused).
  */
 int64_t synth_packed(uint8_t* mask, uint32_t* labels, int64_t nx, int64_t ny, int64_t nz, int ndim,
                      int64_t n_obj, double rmin, double rmax, double f_ell, double f_super,
-                     double shrink_lo, double shrink_hi, uint64_t seed) {
+                     double shrink_lo, double shrink_hi, double grow_max, uint64_t seed) {
   vol_t v = {mask, labels, nx, ny, nz, ndim};
   int64_t n = nx * ny * nz;
   memset(mask, 0, (size_t)n);
@@ -500,6 +612,19 @@ int64_t synth_packed(uint8_t* mask, uint32_t* labels, int64_t nx, int64_t ny, in
   }
   double lo[3] = {0, 0, 0}, hi[3] = {(double)nx, (double)ny, (double)(ndim == 3 ? nz : 1)};
   partition(&P, lo, hi, 0, n_obj);
+  const int grow = grow_max > 1.0;
+  shape_t* shs = NULL;
+  double (*cs)[3] = NULL;
+  uint8_t* placed = NULL;
+  if (grow) {
+    shs = (shape_t*)malloc(sizeof(shape_t) * (size_t)P.ncells);
+    cs = (double(*)[3])malloc(sizeof(double[3]) * (size_t)P.ncells);
+    placed = (uint8_t*)calloc((size_t)P.ncells, 1);
+    if (!shs || !cs || !placed) {
+      free(shs); free(cs); free(placed); free(P.w); free(P.id); free(P.cells);
+      return -1;
+    }
+  }
 
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t ci = 0; ci < P.ncells; ++ci) {
@@ -573,6 +698,11 @@ int64_t synth_packed(uint8_t* mask, uint32_t* labels, int64_t nx, int64_t ny, in
     s *= unif(&rr, shrink_lo, shrink_hi);
     sh.s = s;
     uint32_t label = (uint32_t)(ci + 1);
+    if (grow) {
+      shs[ci] = sh;
+      for (int i = 0; i < 3; ++i) cs[ci][i] = c[i];
+      placed[ci] = 1;
+    }
     for (int64_t z = clo[2]; z < chi[2]; ++z)
       for (int64_t y = clo[1]; y < chi[1]; ++y)
         for (int64_t x = clo[0]; x < chi[0]; ++x)
@@ -582,6 +712,10 @@ int64_t synth_packed(uint8_t* mask, uint32_t* labels, int64_t nx, int64_t ny, in
             labels[i] = label;
           }
   }
+  if (grow) grow_particles(&v, shs, cs, placed, P.ncells, grow_max);
+  free(shs);
+  free(cs);
+  free(placed);
   int64_t out = P.ncells;
   free(P.w);
   free(P.id);
