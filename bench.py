@@ -219,6 +219,10 @@ def measure_batch(lt, args, dev):
                       "sphericity": torch.empty(n, dtype=torch.float32, device=dev),
                       "roundness": torch.empty(n, dtype=torch.float32, device=dev), "n_labels": n})
     nvox = sum(m.size for m, _, _ in vols)
+    # algorithmic bytes of the whole batch: per voxel the EDT passes (x 5, y
+    # 8, z 8 in 3D), the ridge pass's 12 and the shape reduction's 8 (the
+    # 16 B per kept centre left out: the batch reports no centre counts)
+    abytes = sum((41 if m.ndim == 3 else 33) * m.size for m, _, _ in vols)
     del vols
     batch = lt.Batch(items, branches=4)
     cache = os.environ.get("LT_AUTOTUNE_CACHE") or os.path.join(tempfile.mkdtemp(), "autotune.json")
@@ -240,7 +244,10 @@ def measure_batch(lt, args, dev):
     ms_graph = timed(batch.run, args.batch_steps)
     ms_eager = timed(batch.run_eager, max(3, args.batch_steps // 2))
     batch.status()
+    peak, peak_kind = peaks()
     out = {"value": nvox / (ms_graph * 1e-3) / 1e6, "unit": UNIT, "ms_per_batch": ms_graph,
+           "algorithmic_bytes": abytes, "achieved_gbs": abytes / (ms_graph * 1e-3) / 1e9,
+           "frac_hbm": abytes / (ms_graph * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
            "eager_value": nvox / (ms_eager * 1e-3) / 1e6, "eager_ms_per_batch": ms_eager,
            "volumes": len(items), "voxels": nvox, "settings": batch.settings(),
            "workload": "64 cubic volumes, edge U{64..384}, 512^3 mix; 8 x 2D 4096^2 ellipses",
@@ -786,9 +793,25 @@ def main():
         lt.lt_measure_host(mh, lh, n_labels, Sh, Rh, wsh)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = max_over_ranks(e2e_s, dist, dev)
+    # the copy rate alone: the same pinned host bytes into device buffers,
+    # one cudaMemcpyAsync each, no kernels (bounds what the host path can reach)
+    dm = torch.empty(mh.shape, dtype=mh.dtype, device=dev)
+    dl = torch.empty(lh.shape, dtype=lh.dtype, device=dev)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dm.copy_(mh, non_blocking=True)
+    dl.copy_(lh, non_blocking=True)
+    h0.record(stream)
+    for _ in range(3):
+        dm.copy_(mh, non_blocking=True)
+        dl.copy_(lh, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * (mask.nbytes + labels.nbytes) / (h0.elapsed_time(h1) * 1e-3) / 1e9
+    del dm, dl
     e2e = {"value": whole_job_rate(world, nvox, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(mask.nbytes + labels.nbytes),
-           "d2h_bytes_per_step": int(2 * 4 * n_labels)}
+           "d2h_bytes_per_step": int(2 * 4 * n_labels),
+           "ms_per_step": e2e_s * 1e3, "h2d_copy_gbs": h2d_gbs}
 
     # per-kernel roofline: HBM kernels by algorithmic bytes, painting by
     # updates per second against the probed atomic-update ceiling
@@ -825,6 +848,11 @@ def main():
                 "avg_ms": kd["avg_ms"], "algorithmic_bytes": kd.get("algorithmic_bytes"),
                 "peak_source": peak_kind}
     gpu_launches = sum(v[0] for v in trace.values())
+    # the whole step against HBM by the same per-kernel algorithmic bytes
+    # (painting, counted in updates, adds none)
+    step_ab = sum(algorithmic_bytes(k, nvox, n_surv) or 0 for k in trace)
+    step_roof = {"algorithmic_bytes": step_ab, "achieved_gbs": step_ab / (ms * 1e-3) / 1e9,
+                 "frac_hbm": step_ab / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
 
     batched = None
     if not args.no_batch:
@@ -851,7 +879,7 @@ def main():
                           "counters": counters,
                           "seed": args.seed, "parallelism": f"replicas{world}",
                           "l2": "inputs larger than L2 (no flush needed)"},
-               "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "kernels": kernels, "step_roofline": step_roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": gpu_launches, "clocks": clk, "batched": batched, "learned": learned}
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -69,7 +69,7 @@ constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a cr
 constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
 constexpr int kChunkR2D = 64;   // 2D: largest r^2 painted in shared chunks (bigger discs: a warp each)
 constexpr uint32_t kParts = 4096;      // warps sharing one big row-mode centre, at most
-constexpr uint32_t kStepsPerPart = 2;  // row steps (32 rows each) per sharing warp, at least
+constexpr uint32_t kPartWork = 4096;  // row-mode work (voxels) per sharing warp, at least
 
 // Centre records: at most one per voxel, plus the extra part records of the
 // shared row-mode centres (at most n/8). The front list starts at 0, the
@@ -298,8 +298,8 @@ struct RidgeWait {
 
 // The record of kept centre at tile position (tx, ty) of plane zc from its
 // three class keys (see the ridge kernel); also decides which list takes
-// it. Row-mode centres are written to the back of `surv` at once (keepA =
-// keepB = false).
+// it. Row-mode centres shared by several warps are written to the back of
+// `surv` at once (keepA = keepB = false).
 template <int NDIM>
 __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3], int tx, int ty, int zc, int x0,
                                              int y0, const Dims& d, const uint32_t* mt, const uint16_t* sbase,
@@ -349,6 +349,7 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
       if (brn[k] >= 0 && brn[k] - m[k] > bestm) {
         bestm = brn[k] - m[k];
         code = bcode[k];
+        kd = k;
       }
   }
   const int x = x0 + tx, y = y0 + ty;
@@ -380,18 +381,36 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
   keepA = tab && (NDIM == 2 ? r2 <= (uint32_t)kChunkR2D : best <= chunk_cres);
   keepB = !keepA;
   if (keepB && (NDIM == 2 || !tab)) {
-    // painted row by row, written at once (these centres are rare): a big
-    // ball as up to kParts records, one per warp sharing it (w = part | parts <<
-    // 16; about 2 row steps of 32 rows per part), while the extra records fit
-    // their budget of n/8
-    keepB = false;
-    const int side = 2 * (int)isqrt24(r2) + 1;
-    const uint32_t steps = (uint32_t)((NDIM == 3 ? side * side : side) + 31) / 32;  // row steps
-    uint32_t parts = min(kParts, max(1u, steps / kStepsPerPart));
+    // painted row by row. Work: without a dominant the whole ball, else
+    // about 4 voxels' worth per row that can meet the crescent's cap (see
+    // cap_rows: depth along d about R + T / (2 |d|), T = |d|^2 - (rD^2 -
+    // r^2); the rows through a cap of depth t and base radius a number about
+    // pi a^2 + 2 a (t + 3)). A centre with more than kPartWork of it is
+    // written at once as up to kParts records, one per warp sharing it (w =
+    // part | parts << 16), while the extra records fit their budget of n/8;
+    // the others go to the back list like big table crescents.
+    const int R = (int)isqrt24(r2), side = 2 * R + 1;
+    float work;
+    if (code == kNoDominant) {
+      work = NDIM == 3 ? 4.19f * (float)R * (float)R * (float)R : 3.1416f * (float)R * (float)R;
+    } else {
+      float rows = (float)(NDIM == 3 ? side * side : side);
+      if (NDIM == 3 && kd >= 0) {
+        const float dn = sqrtf((float)(kd + 1));
+        const float t = fminf(fmaxf((float)R + (float)(kd + 1 - (brn[kd] - (int)r2)) / (2.0f * dn), 0.0f), (float)side);
+        const float a = sqrtf(fmaxf(t * ((float)side - t), 0.0f));
+        rows = fminf(rows, 3.1416f * a * a + 2.0f * a * (t + 3.0f) + 2.0f * t + 16.0f);
+      }
+      work = 4.0f * rows;
+    }
+    uint32_t parts = min(kParts, max(1u, (uint32_t)(work / (float)kPartWork)));
     if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
-    const uint32_t bb = atomicAdd(&hdr->n_big, parts);
-    for (uint32_t q = 0; q < parts; ++q)
-      surv[record_capacity(d.n) - 1 - (bb + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 16));
+    if (parts > 1) {
+      keepB = false;
+      const uint32_t bb = atomicAdd(&hdr->n_big, parts);
+      for (uint32_t q = 0; q < parts; ++q)
+        surv[record_capacity(d.n) - 1 - (bb + q)] = make_uint4(rec.x, rec.y, rec.z, q | (parts << 16));
+    }
   }
   return rec;
 }
@@ -992,18 +1011,84 @@ __device__ __forceinline__ int owner_lane(int start, int k) {
   return j;
 }
 
-// One row-mode centre, one warp: the lanes take 32 rows (dz, dy) of the
-// ball at a time and compute each row's crescent spans (the row of the ball
-// minus the higher-ranked neighbours' rows, clamped to the array); then the
-// spans' voxels are shared out in order, so consecutive lanes update
-// consecutive x. Part p of `parts` takes the row steps p, p + parts, ...
+// Rows of a row-mode centre that can hold crescent voxels. A voxel u (offset
+// from c) inside B(c) but outside the ball of a neighbour X = c + d has
+// |u|^2 <= r^2 and |u - d|^2 > rX^2, so 2 u.d < |d|^2 - (rX^2 - r^2) =: T:
+// every voxel of B(c) outside that half-space lies in B(X). For the dominant
+// (the neighbour whose ball comes closest to containing c's) the half-space
+// leaves a small cap at the far side of B(c); the extra balls cut it
+// further. Row (oy, oz) holds voxels |ox| <= w = isqrt(r^2 - oy^2 - oz^2),
+// so it can meet the half-space only when 2 (ddy oy + ddz oz) - 2 |ddx| w
+// <= T - 1. cap_clip narrows [lo, hi], the candidate oy at height oz (H =
+// r^2 - oz^2), to the rows that can (a superset: each row's spans are still
+// computed exactly).
+__device__ __forceinline__ void cap_clip(int r2, int H, int ddx, int ddy, int ddz, int r2x, int oz, int& lo,
+                                         int& hi) {
+  const int T = ddx * ddx + ddy * ddy + ddz * ddz - (r2x - r2);
+  if (ddx == 0) {
+    // 2 ddy oy <= T - 1 - 2 ddz oz
+    const int q = (T - 1 - 2 * ddz * oz) >> 1;  // floor
+    if (ddy == 0) {
+      if (q < 0) hi = lo - 1;
+    } else if (ddy > 0) {
+      hi = min(hi, q);
+    } else {
+      lo = max(lo, -q);
+    }
+    return;
+  }
+  // |ddx| = 1: w >= s - K with s = ddy oy + ddz oz, K = floor((T - 1) / 2);
+  // rows with s <= K qualify, the others need oy^2 + (s - K)^2 <= H
+  const int e = ddz * oz - ((T - 1) >> 1);  // s - K = ddy oy + e
+  if (ddy == 0) {
+    if (e <= 0) return;
+    const int H2 = H - e * e;
+    if (H2 < 0) {
+      hi = lo - 1;
+      return;
+    }
+    const int w2 = (int)isqrt24((uint32_t)H2);
+    lo = max(lo, -w2);
+    hi = min(hi, w2);
+    return;
+  }
+  // t = ddy oy: t <= -e, or 2 t^2 + 2 e t + e^2 - H <= 0; the two sets join
+  // into t <= max(-e, (-e + sqrt(2H - e^2)) / 2) within the disc (bound
+  // rounded up by one)
+  int tmax = -e;
+  const int disc = 2 * H - e * e;
+  if (disc >= 0) tmax = max(tmax, (int)floorf((sqrtf((float)disc) - (float)e) * 0.5f) + 1);
+  if (ddy > 0) hi = min(hi, tmax);
+  else lo = max(lo, -tmax);
+}
+
+// The candidate rows at height oz: the disc's rows within [ylo, yhi], cut by
+// the half-spaces of the higher-ranked balls (hr[k] < 0: none).
+__device__ __forceinline__ void cap_rows(const Centre& c, const int hr[3], const int hx[3], const int hy[3],
+                                         const int hz[3], int oz, int ylo, int yhi, int& lo, int& hi) {
+  const int H = (int)c.r2 - oz * oz;
+  const int wy = (int)isqrt24((uint32_t)H);
+  lo = max(-wy, ylo);
+  hi = min(wy, yhi);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (hr[k] >= 0) cap_clip((int)c.r2, H, hx[k], hy[k], hz[k], hr[k], oz, lo, hi);
+}
+
+// One row-mode centre, one warp. The heights oz go 32 at a time, each lane
+// one height and its interval of candidate rows (cap_rows); a warp scan
+// numbers the rows, which are then taken 32 at a time, lane k the k-th row,
+// and each row's crescent spans are computed (the row of the ball minus the
+// higher-ranked neighbours' rows, clamped to the array); then the spans'
+// voxels are shared out in order, so consecutive lanes update consecutive
+// x. Part p of `parts` takes the row groups q (rows 32q .. 32q + 31 in the
+// numbering over all heights) with q = p mod parts.
 template <int NDIM>
 __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int parts, const Dims& d, size_t sy,
                                                   size_t sz, bool touch, const uint32_t* __restrict__ dt2,
                                                   const uint32_t* __restrict__ labels,
                                                   uint32_t* __restrict__ lt2, const PaintLut& L, uint32_t& nupd) {
   const int lane = threadIdx.x & 31;
-  const int side = 2 * c.R + 1, nrows = NDIM == 3 ? side * side : side;
   const int xmin = -c.cx, xmax = d.nx - 1 - c.cx;
   // the higher-ranked balls: dominant first, then the two extras (r^2 -1: none)
   int hr[3], hx[3], hy[3], hz[3];
@@ -1013,29 +1098,27 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int
     const int ec = c.eoff[q];
     hr[q + 1] = c.er2[q], hx[q + 1] = ec % 3 - 1, hy[q + 1] = ec / 3 % 3 - 1, hz[q + 1] = ec / 9 - 1;
   }
-  // row r = r0 + lane as (rq, rr) = (r / side, r % side) in 3D, advanced by
-  // the step without a division
-  const int step = 32 * parts;
-  int rq = 0, rr = 0, sq = 0, sr = 0;
-  if (NDIM == 3) {
-    rq = (part * 32 + lane) / side;
-    rr = part * 32 + lane - rq * side;
-    sq = step / side;
-    sr = step - sq * side;
-  }
-  for (int r0 = part * 32; r0 < nrows; r0 += step) {
-    const int r = r0 + lane;
-    int a1 = 0, n1 = 0, a2 = 0, n2 = 0, w = -1;  // spans [a1, a1 + n1), [a2, a2 + n2) of dx
-    uint32_t rowbase = 0;                        // linear index of (cx, y, z)
-    if (r < nrows) {
-      int dz = 0, dy = r - c.R;  // 2D: one row per dy
-      if (NDIM == 3) {
-        dz = rq - c.R;
-        dy = rr - c.R;
-      }
-      const int z = c.cz + dz, y = c.cy + dy;
-      const int h = (int)c.r2 - dz * dz - dy * dy;
-      if (h >= 0 && z >= 0 && z < d.nz && y >= 0 && y < d.ny) {
+  const int oz_lo = NDIM == 3 ? max(-c.R, -c.cz) : 0, oz_hi = NDIM == 3 ? min(c.R, d.nz - 1 - c.cz) : 0;
+  int row0 = 0;  // number of the first row of this batch of heights
+  for (int oz0 = oz_lo; oz0 <= oz_hi; oz0 += 32) {
+    const int oz = oz0 + lane;
+    int lo = 0, hi = -1;
+    if (oz <= oz_hi) cap_rows(c, hr, hx, hy, hz, oz, -c.cy, d.ny - 1 - c.cy, lo, hi);
+    int nrows;
+    const int rstart = warp_starts(max(0, hi - lo + 1), lane, &nrows);
+    // this part's row groups among rows row0 .. row0 + nrows - 1
+    const int qa = row0 >> 5, qb = (row0 + nrows - 1) >> 5;
+    int q = qa + ((part - qa) % parts + parts) % parts;
+    for (; nrows > 0 && q <= qb; q += parts) {
+      const int k = 32 * q + lane - row0;  // row of this batch taken by the lane
+      int a1 = 0, n1 = 0, a2 = 0, n2 = 0, w = -1;  // spans [a1, a1 + n1), [a2, a2 + n2) of dx
+      uint32_t rowbase = 0;                        // linear index of (cx, y, z)
+      const int j = owner_lane(rstart, max(0, min(k, nrows - 1)));
+      const int dz = __shfl_sync(kFull, oz, j);
+      const int dy = __shfl_sync(kFull, lo, j) + (k - __shfl_sync(kFull, rstart, j));
+      if (k >= 0 && k < nrows) {
+        const int z = c.cz + dz, y = c.cy + dy;
+        const int h = (int)c.r2 - dz * dz - dy * dy;
         w = isqrt_lut(L, h);
         // this row of the higher-ranked balls as one interval [elo, ehi] of
         // dx: an extra's row joins only when it touches the interval so far
@@ -1043,18 +1126,18 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int
         // voxels)
         int elo = 1, ehi = 0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (hr[q] < 0) continue;
-          const int hd = hr[q] - (dz - hz[q]) * (dz - hz[q]) - (dy - hy[q]) * (dy - hy[q]);
+        for (int e = 0; e < 3; ++e) {
+          if (hr[e] < 0) continue;
+          const int hd = hr[e] - (dz - hz[e]) * (dz - hz[e]) - (dy - hy[e]) * (dy - hy[e]);
           if (hd < 0) continue;
           const int wd = isqrt_lut(L, hd);
-          const int lo = hx[q] - wd, hi = hx[q] + wd;
+          const int elo2 = hx[e] - wd, ehi2 = hx[e] + wd;
           if (elo > ehi) {
-            elo = lo;
-            ehi = hi;
-          } else if (lo <= ehi + 1 && hi >= elo - 1) {
-            elo = min(elo, lo);
-            ehi = max(ehi, hi);
+            elo = elo2;
+            ehi = ehi2;
+          } else if (elo2 <= ehi + 1 && ehi2 >= elo - 1) {
+            elo = min(elo, elo2);
+            ehi = max(ehi, ehi2);
           }
         }
         int hi1 = w, lo2 = 1, hi2 = 0;
@@ -1070,32 +1153,25 @@ __device__ __forceinline__ void paint_centre_rows(const Centre& c, int part, int
         if (w * w != h) w = -1;  // only the ends of an exact row can be background
         rowbase = (uint32_t)((size_t)z * sz + (size_t)y * sy + (size_t)c.cx);
       }
-    }
-    if (NDIM == 3) {
-      rr += sr;
-      rq += sq;
-      if (rr >= side) {
-        rr -= side;
-        ++rq;
+      int total;
+      const int start = warp_starts(n1 + n2, lane, &total);
+      for (int kb = 0; kb < total; kb += 32) {
+        const int kk = kb + lane;
+        const int jj = owner_lane(start, kk);
+        const int o = kk - __shfl_sync(kFull, start, jj);
+        const int a1j = __shfl_sync(kFull, a1, jj), n1j = __shfl_sync(kFull, n1, jj);
+        const int a2j = __shfl_sync(kFull, a2, jj), wj = __shfl_sync(kFull, w, jj);
+        const uint32_t rb = __shfl_sync(kFull, rowbase, jj);
+        if (kk >= total) continue;
+        const int dx = o < n1j ? a1j + o : a2j + (o - n1j);
+        const uint32_t i = rb + (uint32_t)dx;  // modulo 2^32: the sum is in range
+        if (wj >= 0 && (dx == wj || dx == -wj) && dt2[i] == 0) continue;
+        if (touch && labels[i] != c.label) continue;
+        atomicMax(lt2 + i, c.r2);
+        ++nupd;
       }
     }
-    int total;
-    const int start = warp_starts(n1 + n2, lane, &total);
-    for (int kb = 0; kb < total; kb += 32) {
-      const int k = kb + lane;
-      const int j = owner_lane(start, k);
-      const int o = k - __shfl_sync(kFull, start, j);
-      const int a1j = __shfl_sync(kFull, a1, j), n1j = __shfl_sync(kFull, n1, j);
-      const int a2j = __shfl_sync(kFull, a2, j), wj = __shfl_sync(kFull, w, j);
-      const uint32_t rb = __shfl_sync(kFull, rowbase, j);
-      if (k >= total) continue;
-      const int dx = o < n1j ? a1j + o : a2j + (o - n1j);
-      const uint32_t i = rb + (uint32_t)dx;  // modulo 2^32: the sum is in range
-      if (wj >= 0 && (dx == wj || dx == -wj) && dt2[i] == 0) continue;
-      if (touch && labels[i] != c.label) continue;
-      atomicMax(lt2 + i, c.r2);
-      ++nupd;
-    }
+    row0 += nrows;
   }
 }
 
