@@ -243,13 +243,20 @@ def measure_batch(lt, args, dev):
 
     ms_graph = timed(batch.run, args.batch_steps)
     ms_eager = timed(batch.run_eager, max(3, args.batch_steps // 2))
+    # where an eager run's time goes, per kernel name (launches on parallel
+    # branches overlap, so the sum can exceed the run)
+    lt.lt_trace_enable(True)
+    batch.run_eager()
+    torch.cuda.synchronize()
+    stages = {k: round(v[1], 4) for k, v in lt.lt_trace_summary().items()}
+    lt.lt_trace_enable(False)
     batch.status()
     peak, peak_kind = peaks()
     out = {"value": nvox / (ms_graph * 1e-3) / 1e6, "unit": UNIT, "ms_per_batch": ms_graph,
            "algorithmic_bytes": abytes, "achieved_gbs": abytes / (ms_graph * 1e-3) / 1e9,
            "frac_hbm": abytes / (ms_graph * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
            "eager_value": nvox / (ms_eager * 1e-3) / 1e6, "eager_ms_per_batch": ms_eager,
-           "volumes": len(items), "voxels": nvox, "settings": batch.settings(),
+           "volumes": len(items), "voxels": nvox, "settings": batch.settings(), "eager_stage_ms": stages,
            "workload": "64 cubic volumes, edge U{64..384}, 512^3 mix; 8 x 2D 4096^2 ellipses",
            "generate_s": gen_s}
     batch.close()

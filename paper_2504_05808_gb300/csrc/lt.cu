@@ -28,11 +28,11 @@
 // signed permutation of the axes maps it onto the crescent of the canonical
 // offset of d's class, (1,0,0), (1,1,0) or (1,1,1). A kept centre has
 // r_c^2 <= r_D^2 < M(d, r_c^2), about 2 |d| r_c values of r_D^2, so for
-// r_c^2 <= 200 every crescent fits a table of 3.1 M voxel offsets. Such a
+// r_c^2 <= 324 every crescent fits a table of 10.4 M voxel offsets. Such a
 // centre paints its tabulated crescent voxel by voxel (lanes of a warp share
 // the voxels of 32 centres). The dominant neighbour D is the one whose
 // crescent is smallest (for larger radii: the one whose ball comes closest to
-// containing c's). Centres with r^2 > 200, without a higher-ranked neighbour,
+// containing c's). Centres with r^2 > 324, without a higher-ranked neighbour,
 // or in 2D paint row by row instead.
 //
 // Voxels strictly inside B(c) are foreground (DT2(c) is the distance to the
@@ -61,15 +61,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kMCap = 1u << 18;  // containment table covers r^2 <= 2^18
-constexpr int kCresT = 200;           // crescent tables cover r^2 <= 200
-constexpr int kCresMaxCombos = 16384;
-constexpr int kCresMaxVoxels = 5 * 1024 * 1024;  // both orderings (about 4.8 M voxels)
+constexpr int kCresT = 324;           // crescent tables cover r^2 <= 324
+constexpr int kCresMaxCombos = 1 << 15;
+constexpr int kCresMaxVoxels = 16 * 1024 * 1024;  // both orderings (about 15.6 M voxels)
 constexpr uint32_t kNoDominant = 31u;
 constexpr uint32_t kTableRecord = 1u << 31;  // record z flag: painted from a crescent table
 constexpr int kChunkCres = 64;  // largest crescent painted in shared chunks
 constexpr int kChunkR2D = 64;   // 2D: largest r^2 painted in shared chunks (bigger discs: a warp each)
 constexpr uint32_t kParts = 4096;      // warps sharing one big row-mode centre, at most
-constexpr uint32_t kPartWork = 4096;  // row-mode work (voxels) per sharing warp, at least
+constexpr uint32_t kPartWork = 1024;  // row-mode work (voxels) per sharing warp, at least
 
 // Centre records: at most one per voxel, plus the extra part records of the
 // shared row-mode centres (at most n/8). The front list starts at 0, the
@@ -80,8 +80,8 @@ constexpr int kNoTable = 0x3FFFFFFF;  // "never contained" beyond the table
 __device__ uint32_t g_m3[3 * (kMCap + 1)];  // M for offset classes 1..3 (3D)
 __device__ uint32_t g_m2[2 * (kMCap + 1)];  // M for offset classes 1..2 (2D)
 __device__ uint32_t g_cres_base[3 * (kCresT + 1)];  // first combination of (class, r^2)
-// per combination: x = first voxel | (size & 511) << 23, y = first voxel of
-// the same crescent in the alternative order below | (size >> 9) << 23
+// per combination: x = first voxel | (size & 255) << 24, y = first voxel of
+// the same crescent in the alternative order below | (size >> 8) << 24
 __device__ uint2 g_cres_combo[kCresMaxCombos];
 // (the same crescents with another canonical axis innermost: y for class 1,
 // z for class 2; class 3 has one order)
@@ -189,10 +189,10 @@ HostTables* build_host_tables() {
   // table records hold a crescent's size in 11 bits; the ridge kernel keeps
   // the first combination of each (class, r^2) in 16 bits
   for (size_t i = 0; i + 1 < t->start.size(); ++i) t->ok = t->ok && t->start[i + 1] - t->start[i] < 2048u;
-  t->ok = t->ok && t->start.size() < (1u << 16) && t->vox.size() < (1u << 23);
+  t->ok = t->ok && t->start.size() < (1u << 16) && t->vox.size() < (1u << 24);
   for (size_t i = 0; i + 1 < t->start.size(); ++i) {
     const uint32_t size = t->start[i + 1] - t->start[i];
-    t->combo.push_back(make_uint2(t->start[i] | ((size & 511u) << 23), t->start_alt[i] | ((size >> 9) << 23)));
+    t->combo.push_back(make_uint2(t->start[i] | ((size & 255u) << 24), t->start_alt[i] | ((size >> 8) << 24)));
   }
   return t;
 }
@@ -266,10 +266,10 @@ __device__ __forceinline__ uint32_t cres_combo(const uint16_t* base, int cls, ui
 // crescents and the centres painted row by row.
 // Records (uint4). Offset codes: (dz+1)*9 + (dy+1)*3 + (dx+1), 31 for none.
 //   Table centres (3D): x = linear index; y = first crescent voxel; z = r^2 |
-//   dominant code << 8 | codes of up to two more higher-ranked same-label
-//   neighbours << 13 (5 bits each) | ball inside the array << 23 |
-//   kTableRecord; w = those two neighbours' r^2 (8 bits each, 0xFF none) |
-//   crescent size << 16.
+//   dominant code << 9 | codes of up to two more higher-ranked same-label
+//   neighbours << 14 (5 bits each) | ball inside the array << 24 |
+//   kTableRecord; w = those two neighbours' r^2 (9 bits each, 0x1FF none) |
+//   crescent size << 18.
 //   Painting needs no other lookup.
 //   Row centres and 2D: x = linear index, y = r^2 | dominant code << 25,
 //   z = the two extra codes; w = part | parts << 16 (row-mode centres go to
@@ -281,7 +281,7 @@ constexpr int kOX = 4;                             // halo column of x0 (keeps T
 constexpr int kBX = kTX + 2 * kOX, kBY = kTY + 2;  // TMA box: 72 x 10 words
 constexpr int kSlotPitch = 736;                    // words per slot: 72 x 10 rounded up to 128 bytes
 constexpr int kSlots = 4;                          // planes z-2 .. z in use, z+1 in flight
-constexpr int kListBuf = 896;  // kept centres buffered per CTA (a plane adds at most kTile)
+constexpr int kListBuf = 832;  // kept centres buffered per CTA (a plane adds at most kTile)
 constexpr int kKeptQ = 128;    // kept voxels per plane handed from stage 2 to stage 3
 constexpr uint32_t kPlaneBytes = kBX * kBY * 4;
 static_assert(kSlotPitch * 4 % 128 == 0 && kSlotPitch >= kBX * kBY, "slot layout");
@@ -327,10 +327,10 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
       ce[k] = brn[k] >= 0 ? g_cres_combo[cres_combo(sbase, k, r2, (uint32_t)brn[k])] : make_uint2(0u, 0u);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const uint32_t sz = (ce[k].x >> 23) | ((ce[k].y >> 23) << 9);
+      const uint32_t sz = (ce[k].x >> 24) | ((ce[k].y >> 24) << 8);
       if (brn[k] >= 0 && sz < best) {
         best = sz;
-        vstart = (bcode[k] % 3 == 1 ? ce[k].y : ce[k].x) & 0x7FFFFFu;
+        vstart = (bcode[k] % 3 == 1 ? ce[k].y : ce[k].x) & 0xFFFFFFu;
         code = bcode[k];
         kd = k;
       }
@@ -355,13 +355,13 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
   const int x = x0 + tx, y = y0 + ty;
   const uint32_t v = (uint32_t)(((size_t)zc * d.ny + (size_t)y) * d.nx + (size_t)x);
   // the other classes' candidates: extra balls a crescent voxel may lie in,
-  // with their r^2 (below M(d, r^2) <= 252 for table centres)
-  uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0xFFFFu, ne = 0;
+  // with their r^2 (below M(d, r^2) < 400 for table centres; 9 bits each)
+  uint32_t extra = kNoDominant | (kNoDominant << 5), er = 0x3FFFFu, ne = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
     if (NDIM == 3 && k != kd && brn[k] >= 0 && ne < 2) {
       extra = (extra & ~(31u << (5 * ne))) | (bcode[k] << (5 * ne));
-      er = (er & ~(0xFFu << (8 * ne))) | ((uint32_t)min(brn[k], 0xFE) << (8 * ne));
+      er = (er & ~(0x1FFu << (9 * ne))) | ((uint32_t)min(brn[k], 0x1FE) << (9 * ne));
       ++ne;
     }
   const bool tab = NDIM == 2 || (r2 <= (uint32_t)kCresT && code != kNoDominant);
@@ -373,7 +373,7 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
       return (int64_t)r2 < (int64_t)(vv + 1) * (vv + 1) && (int64_t)r2 < (int64_t)(nv - vv) * (nv - vv);
     };
     const uint32_t inside = fits(x, d.nx) && fits(y, d.ny) && fits(zc, d.nz);
-    rec = make_uint4(v, vstart, r2 | (code << 8) | (extra << 13) | (inside << 23) | kTableRecord, er | (best << 16));
+    rec = make_uint4(v, vstart, r2 | (code << 9) | (extra << 14) | (inside << 24) | kTableRecord, er | (best << 18));
   } else {
     rec = make_uint4(v, r2 | (code << 25), extra, 0u);
   }
@@ -385,10 +385,11 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
     // about 4 voxels' worth per row that can meet the crescent's cap (see
     // cap_rows: depth along d about R + T / (2 |d|), T = |d|^2 - (rD^2 -
     // r^2); the rows through a cap of depth t and base radius a number about
-    // pi a^2 + 2 a (t + 3)). A centre with more than kPartWork of it is
-    // written at once as up to kParts records, one per warp sharing it (w =
-    // part | parts << 16), while the extra records fit their budget of n/8;
-    // the others go to the back list like big table crescents.
+    // pi a^2 + 2 a (t + 3)). A centre with more than kPartWork of it per
+    // warp (8 kPartWork with a dominant) is written at once as up to kParts
+    // records, one per warp sharing it (w = part | parts << 16), while the
+    // extra records fit their budget of n/8; the others go to the back list
+    // like big table crescents.
     const int R = (int)isqrt24(r2), side = 2 * R + 1;
     float work;
     if (code == kNoDominant) {
@@ -403,7 +404,10 @@ __device__ __forceinline__ uint4 make_record(uint32_t r2, const uint32_t kmax[3]
       }
       work = 4.0f * rows;
     }
-    uint32_t parts = min(kParts, max(1u, (uint32_t)(work / (float)kPartWork)));
+    // (a cap's rows are mostly cut further by the extra balls, so a centre
+    // with a dominant is split only when its cap is very large)
+    const float per_part = code == kNoDominant ? (float)kPartWork : 8.0f * (float)kPartWork;
+    uint32_t parts = min(kParts, max(1u, (uint32_t)(work / per_part)));
     if (parts > 1 && atomicAdd(&hdr->n_extra, parts - 1) + (parts - 1) > d.n / 8) parts = 1;
     if (parts > 1) {
       keepB = false;
@@ -901,9 +905,9 @@ __device__ __forceinline__ int isqrt_lut(const PaintLut& L, int v) {
 // as two 16-byte words (idx, vstart, start, r2ax) and (S, ex), plus the label.
 struct TabCentre {
   uint32_t idx, vstart, start;
-  uint32_t r2ax;  // r^2 | world axis (2 bits each) and sign bit (<< 6..8) of canonical x, y, z << 8 | inside << 17
+  uint32_t r2ax;  // r^2 | world axis (2 bits each) and sign bit (<< 6..8) of canonical x, y, z << 9 | inside << 18
   int S[3];       // signed linear strides of the canonical axes x, y, z
-  uint32_t ex;    // extra balls: r^2 (8 bits each, 0xFF none) | canonical offsets << 16 (6 bits each)
+  uint32_t ex;    // extra balls: r^2 (9 bits each, 0x1FF none) | canonical offsets << 18 (6 bits each)
   uint32_t label;
 };
 
@@ -914,9 +918,9 @@ __device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, 
   c.idx = rec.x;
   c.vstart = rec.y;
   c.start = 0;
-  const uint32_t code = (rec.z >> 8) & 31u;
+  const uint32_t code = (rec.z >> 9) & 31u;
   const uint32_t pm = L.perm[code];
-  c.r2ax = (rec.z & 0xFFu) | (pm << 8) | (((rec.z >> 23) & 1u) << 17);
+  c.r2ax = (rec.z & 0x1FFu) | (pm << 9) | (((rec.z >> 24) & 1u) << 18);
   const int sy_ = (int)sy, sz_ = (int)sz;
   auto stride = [&](uint32_t a, uint32_t g) {
     const int t = a == 0 ? 1 : (a == 1 ? sy_ : sz_);
@@ -928,17 +932,17 @@ __device__ __forceinline__ int make_tab_centre(uint4 rec, size_t sy, size_t sz, 
   uint32_t ex = 0;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const uint32_t ec = (rec.z >> (13 + 5 * q)) & 31u;
-    uint32_t er = (rec.w >> (8 * q)) & 0xFFu, eo = 0;
+    const uint32_t ec = (rec.z >> (14 + 5 * q)) & 31u;
+    uint32_t er = (rec.w >> (9 * q)) & 0x1FFu, eo = 0;
     if (ec == kNoDominant)
-      er = 0xFFu;
+      er = 0x1FFu;
     else
       eo = L.eo[code * 27 + ec];
-    ex |= (er << (8 * q)) | (eo << (16 + 6 * q));
+    ex |= (er << (9 * q)) | (eo << (18 + 6 * q));
   }
   c.ex = ex;
   c.label = touch ? labels[c.idx] : 0u;
-  return (int)((rec.w >> 16) & 0x7FFu);
+  return (int)((rec.w >> 18) & 0x7FFu);
 }
 
 // Linear index of canonical crescent voxel p of c; false when the voxel lies
@@ -950,12 +954,12 @@ __device__ __forceinline__ bool tab_voxel_index(const TabCentre& c, uint32_t p, 
   const uint32_t ex = c.ex;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int er = (int)((ex >> (8 * q)) & 0xFFu);
-    const uint32_t eo = (ex >> (16 + 6 * q)) & 63u;
+    const int er = (int)((ex >> (9 * q)) & 0x1FFu);
+    const uint32_t eo = (ex >> (18 + 6 * q)) & 63u;
     const int e0 = (int)(eo & 3u) - 1, e1 = (int)((eo >> 2) & 3u) - 1, e2 = (int)((eo >> 4) & 3u) - 1;
-    if (er != 0xFF && (o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= er) return false;
+    if (er != 0x1FF && (o0 - e0) * (o0 - e0) + (o1 - e1) * (o1 - e1) + (o2 - e2) * (o2 - e2) <= er) return false;
   }
-  const uint32_t axes = c.r2ax >> 8;
+  const uint32_t axes = c.r2ax >> 9;
   if (!(axes & 512u)) {  // the ball may leave the array: check each coordinate
     const int cx = (int)(c.idx % (uint32_t)d.nx);
     const uint32_t t = c.idx / (uint32_t)d.nx;
@@ -1196,11 +1200,11 @@ __device__ __forceinline__ void paint_tab_pair(const TabCentre& c0, int k0, bool
     w1 = w1 && labels[i1] == c1.label;
   }
   if (w0 && b0) {
-    atomicMax(lt2 + i0, c0.r2ax & 0xFFu);
+    atomicMax(lt2 + i0, c0.r2ax & 0x1FFu);
     ++ntab;
   }
   if (w1 && b1) {
-    atomicMax(lt2 + i1, c1.r2ax & 0xFFu);
+    atomicMax(lt2 + i1, c1.r2ax & 0x1FFu);
     ++ntab;
   }
 }

@@ -298,12 +298,17 @@ def test_repeated_calls_reuse_workspace(lt):
         assert_close(R.cpu().numpy(), R_ref, "R")
 
 
-def test_crescent_table_bounds(lt):
-    """Rotated ellipsoids whose inscribed-ball radii run across the edge of
-    the tabulated crescents (r^2 = 200): kept centres on both sides of it,
-    painted from tables and row by row, next to each other in one object."""
+@pytest.mark.parametrize("bound", [200, 324])
+def test_crescent_table_bounds(lt, bound):
+    """Rotated ellipsoids whose inscribed-ball radii run up to and across the
+    edge of the tabulated crescents (r^2 = 324; 200 was the edge of an
+    earlier, smaller table): kept centres on both sides of it, painted from
+    tables and row by row, next to each other in one object."""
     rng = np.random.default_rng(7)
-    for axes in [(14.5, 17.0, 18.0), (14.3, 16.5, 22.0), (14.9, 14.9, 25.0)]:
+    sets = {200: [(14.5, 17.0, 18.0), (14.3, 16.5, 22.0), (14.9, 14.9, 25.0)],
+            324: [(18.5, 21.0, 22.0), (18.3, 20.5, 26.0), (18.9, 18.9, 30.0)]}
+    lo = {200: 144, 324: 256}[bound]
+    for axes in sets[bound]:
         n = int(2 * max(axes)) + 5
         g = np.indices((n, n, n)).reshape(3, -1).T - (n - 1) / 2.0
         q = rng.normal(size=4)
@@ -316,7 +321,7 @@ def test_crescent_table_bounds(lt):
         mask = (((u / np.array(axes)) ** 2).sum(1) <= 1.0).reshape(n, n, n).astype(np.uint8)
         d, _ = check_full(lt, mask, mask.astype(np.uint32), 2)
         r2 = d[mask > 0]
-        assert r2.max() > 200 and np.count_nonzero((r2 > 144) & (r2 <= 200)) > 0
+        assert r2.max() > bound and np.count_nonzero((r2 > lo) & (r2 <= bound)) > 0
 
 
 @pytest.mark.parametrize("shape", [(64, 80), (64, 81), (4, 16, 80)])
