@@ -1214,7 +1214,7 @@ __device__ __forceinline__ void paint_tab_pair(const TabCentre& c0, int k0, bool
 // counter sees few atomics while much work is left, and the last items still
 // spread over all warps one at a time.
 struct WorkGrab {
-  uint32_t next = 0, end = 0;
+  uint32_t next = 0, end = 0, first = 0;  // [first, end): the warp's current range
   __device__ __forceinline__ bool take(unsigned int* ctr, uint32_t items, uint32_t cap, uint32_t& item) {
     if (next == end) {
       const uint32_t warps = gridDim.x * (blockDim.x / 32);
@@ -1223,6 +1223,7 @@ struct WorkGrab {
       uint32_t b = 0;
       if ((threadIdx.x & 31) == 0) b = atomicAdd(ctr, g);
       next = __shfl_sync(kFull, b, 0);
+      first = next;
       end = next + g;
     }
     if (next >= items) return false;
@@ -1231,12 +1232,22 @@ struct WorkGrab {
   }
 };
 constexpr uint32_t kChunkGrab = 8;  // phase 2 chunks per counter update, at most
-constexpr uint32_t kBigGrab = 8;    // phase 1 centres per counter update, at most
+constexpr uint32_t kBigGrab = 8;    // phase 1 centres per counter update, at most (<= 32)
 
-// Phase 2 in 3D: chunk ch of 32 table centres (of n in the front list);
-// the lanes share the chunk's crescent voxels, two per lane in flight.
-__device__ __forceinline__ void paint_table_chunk(const uint4* __restrict__ surv, uint32_t n, uint32_t ch,
-                                                  const Dims& d, size_t sy, size_t sz, bool touch,
+// The record of phase-1 item b, from `held` (lane j holds the record of
+// item first + j of the warp's range, loaded when the range was taken: one
+// load for all instead of one dependent load per item).
+__device__ __forceinline__ uint4 held_record(const uint4& held, uint32_t b, uint32_t first) {
+  const int j = (int)(b - first);
+  return make_uint4(__shfl_sync(kFull, held.x, j), __shfl_sync(kFull, held.y, j), __shfl_sync(kFull, held.z, j),
+                    __shfl_sync(kFull, held.w, j));
+}
+
+// Phase 2 in 3D: chunk ch of 32 table centres (of n in the front list),
+// lane j holding the record of centre 32 ch + j in `rec`; the lanes share
+// the chunk's crescent voxels, two per lane in flight.
+__device__ __forceinline__ void paint_table_chunk(const uint4& rec, uint32_t n, uint32_t ch, const Dims& d,
+                                                  size_t sy, size_t sz, bool touch,
                                                   const uint32_t* __restrict__ dt2,
                                                   const uint32_t* __restrict__ labels, uint32_t* __restrict__ lt2,
                                                   const PaintLut& L, uint32_t& ntab) {
@@ -1246,7 +1257,7 @@ __device__ __forceinline__ void paint_table_chunk(const uint4* __restrict__ surv
   const uint32_t i = ch * 32 + lane;
   int cnt = 0;
   TabCentre mine;
-  if (i < n) cnt = make_tab_centre(surv[i], sy, sz, touch, labels, L, mine);
+  if (i < n) cnt = make_tab_centre(rec, sy, sz, touch, labels, L, mine);
   int total;
   const int start = warp_starts(cnt, lane, &total);
   if (i < n) {
@@ -1345,19 +1356,36 @@ __global__ void __launch_bounds__(256) lt_paint_kernel(const uint4* __restrict__
   {
     WorkGrab grab;
     uint32_t b = 0;
-    while (grab.take(&hdr->ctr_big, nbig, kBigGrab, b))
-      paint_big<NDIM>(surv[record_capacity(d.n) - 1 - b], d, sy, sz, touch, dt2, labels, lt2, lut, nupd, ntab);
+    uint4 held = make_uint4(0u, 0u, 0u, 0u);
+    while (grab.take(&hdr->ctr_big, nbig, kBigGrab, b)) {
+      if (b == grab.first) {  // a new range (uniform in the warp): its records in one go
+        const uint32_t k = b + (uint32_t)lane;
+        if (k < grab.end && k < nbig) held = surv[record_capacity(d.n) - 1 - k];
+      }
+      paint_big<NDIM>(held_record(held, b, grab.first), d, sy, sz, touch, dt2, labels, lt2, lut, nupd, ntab);
+    }
   }
   {
     const uint32_t nchunks = (n + 31) / 32;
     WorkGrab grab;
     uint32_t ch = 0;
+    uint4 next = make_uint4(0u, 0u, 0u, 0u);  // lane j: record j of chunk ch + 1 (3D), loaded ahead
     // 2D chunks vary most in cost: one at a time
     while (grab.take(&hdr->ctr_small, nchunks, NDIM == 3 ? kChunkGrab : 1u, ch)) {
-      if (NDIM == 3)
-        paint_table_chunk(surv, n, ch, d, sy, sz, touch, dt2, labels, lt2, lut, ntab);
-      else
+      if (NDIM == 3) {
+        uint4 rec = next;
+        if (ch == grab.first) {  // a new range (uniform in the warp)
+          const uint32_t i = ch * 32 + (uint32_t)lane;
+          rec = i < n ? surv[i] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (ch + 1 < grab.end) {  // the next chunk's records fly while this one is painted
+          const uint32_t i = (ch + 1) * 32 + (uint32_t)lane;
+          next = i < n ? surv[i] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        paint_table_chunk(rec, n, ch, d, sy, sz, touch, dt2, labels, lt2, lut, ntab);
+      } else {
         paint_row_chunk(surv, n, ch, d, sy, sz, touch, dt2, labels, lt2, nupd);
+      }
     }
   }
 #pragma unroll
@@ -1436,13 +1464,22 @@ __global__ void __launch_bounds__(256) lt_paint_multi_kernel(MultiArgs m, uint32
   {
     WorkGrab grab;
     uint32_t b = 0;
+    uint4 held = make_uint4(0u, 0u, 0u, 0u);
     while (grab.take(&ctr[0], big0[m.nvol], kBigGrab, b)) {
+      if (b == grab.first) {  // a new range (uniform in the warp): its records in one go
+        const uint32_t k = b + (uint32_t)lane;
+        if (k < grab.end && k < big0[m.nvol]) {
+          const int vk = vol_of(big0, k);
+          const VolParams& pk = m.vols[vk];
+          held = reinterpret_cast<const uint4*>(pk.body)[record_capacity(pk.d.n) - 1 - (k - big0[vk])];
+        }
+      }
+      const uint4 rec = held_record(held, b, grab.first);
       const int v = vol_of(big0, b);
       const VolParams& p = m.vols[v];
       const bool touch = *(volatile const uint32_t*)&p.hdr->touch != 0;
-      const uint4* surv = reinterpret_cast<const uint4*>(p.body);
-      paint_big<NDIM>(surv[record_capacity(p.d.n) - 1 - (b - big0[v])], p.d, (size_t)p.d.nx,
-                      (size_t)p.d.nx * p.d.ny, touch, p.dt2, p.labels, p.lt2, lut, nupd, ntab);
+      paint_big<NDIM>(rec, p.d, (size_t)p.d.nx, (size_t)p.d.nx * p.d.ny, touch, p.dt2, p.labels, p.lt2, lut, nupd,
+                      ntab);
     }
   }
   {
@@ -1455,8 +1492,11 @@ __global__ void __launch_bounds__(256) lt_paint_multi_kernel(MultiArgs m, uint32
       const uint4* surv = reinterpret_cast<const uint4*>(p.body);
       const uint32_t n = *(volatile const uint32_t*)&p.hdr->n_surv;
       const size_t sy = (size_t)p.d.nx, sz = (size_t)p.d.nx * p.d.ny;
-      if (NDIM == 3)
-        paint_table_chunk(surv, n, ch - chunk0[v], p.d, sy, sz, touch, p.dt2, p.labels, p.lt2, lut, ntab);
+      if (NDIM == 3) {
+        const uint32_t i = (ch - chunk0[v]) * 32 + (uint32_t)lane;
+        const uint4 rec = i < n ? surv[i] : make_uint4(0u, 0u, 0u, 0u);
+        paint_table_chunk(rec, n, ch - chunk0[v], p.d, sy, sz, touch, p.dt2, p.labels, p.lt2, lut, ntab);
+      }
       else
         paint_row_chunk(surv, n, ch - chunk0[v], p.d, sy, sz, touch, p.dt2, p.labels, p.lt2, nupd);
     }
