@@ -83,22 +83,26 @@ __device__ __forceinline__ void edt_rows_body(const uint8_t* __restrict__ mask, 
   uint16_t* orow = out + (size_t)row * nx;
   const int nseg = (nx + kSeg - 1) / kSeg;  // <= 16
 
-  // First background position of each segment, held by lane == segment.
-  int segfirst = kBig;
-  for (int s = 0; s < nseg; ++s) {
-    const int x0 = s * kSeg + lane * 16;
-    const uint32_t z = VEC ? zero_bits<true>(mrow, x0, nx) : zero_bits_staged(mrow, s * kSeg, nx, stage_m[wid]);
-    int f = z ? x0 + __ffs(z) - 1 : kBig;
+  // First background position of each segment, held by lane == segment, and
+  // the inclusive suffix minimum over segments (lane i: min over segments
+  // >= i); a row of one segment needs neither.
+  int suf = kBig;
+  if (nseg > 1) {  // uniform per warp
+    int segfirst = kBig;
+    for (int s = 0; s < nseg; ++s) {
+      const int x0 = s * kSeg + lane * 16;
+      const uint32_t z = VEC ? zero_bits<true>(mrow, x0, nx) : zero_bits_staged(mrow, s * kSeg, nx, stage_m[wid]);
+      int f = z ? x0 + __ffs(z) - 1 : kBig;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) f = min(f, __shfl_xor_sync(kFull, f, o));
-    if (lane == s) segfirst = f;
-  }
-  // Inclusive suffix minimum over segments (lane i: min over segments >= i).
-  int suf = segfirst;
+      for (int o = 16; o; o >>= 1) f = min(f, __shfl_xor_sync(kFull, f, o));
+      if (lane == s) segfirst = f;
+    }
+    suf = segfirst;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_down_sync(kFull, suf, o);
-    if (lane + o < 32) suf = min(suf, t);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_down_sync(kFull, suf, o);
+      if (lane + o < 32) suf = min(suf, t);
+    }
   }
 
   int carry_left = -1;  // last background before the segment (virtual at -1)

@@ -483,16 +483,33 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
   };
   // without TMA: asynchronous 4-byte copies of the halo plane (zeros outside
   // the array), one commit group per plane
+  // (a thread's halo positions i = tid + 256 k are the same in every plane:
+  // their shared-memory index and in-plane offset, -1 outside the array, are
+  // worked out once)
+  constexpr int kHalo = (kTX + 2) * kBY, kPerThread = (kHalo + 255) / 256;
+  int hoff[kPerThread];
+  uint32_t hdst = 0;  // shared-memory indices, 10 bits each
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int i = tid + 256 * k;
+    const int hx = i % (kTX + 2), hy = i / (kTX + 2);
+    const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+    hoff[k] = i < kHalo && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny ? gy * d.nx + gx : -1;
+    hdst |= (uint32_t)(i < kHalo ? hy * kBX + hx + kOX - 1 : 0) << (10 * k);
+  }
+  static_assert(kPerThread <= 3 && kBX * kBY <= 1024, "halo positions per thread, index bits");
   auto load_plane = [&](int z) {
     const int s = slot_of(z);
-    for (int i = tid; i < (kTX + 2) * kBY; i += 256) {
-      const int hx = i % (kTX + 2), hy = i / (kTX + 2);
-      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      const bool in = z >= 0 && z < d.nz && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-      const size_t g = in ? (size_t)z * plane + (size_t)gy * d.nx + gx : 0;
-      cp_async4(&sD[s][hy * kBX + hx + kOX - 1], dt2 + g, in);
-      cp_async4(&sL[s][hy * kBX + hx + kOX - 1], labels + g, in);
-    }
+    const bool zin = z >= 0 && z < d.nz;
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k)
+      if (tid + 256 * k < kHalo) {
+        const bool in = zin && hoff[k] >= 0;
+        const size_t g = in ? (size_t)z * plane + (size_t)hoff[k] : 0;
+        const int dst = (int)((hdst >> (10 * k)) & 1023u);
+        cp_async4(&sD[s][dst], dt2 + g, in);
+        cp_async4(&sL[s][dst], labels + g, in);
+      }
     cp_async_commit();
   };
   // appends records to the shared buffer: list A from its front, list B
@@ -534,6 +551,8 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
   } else {
     load_plane(z0 - 1);
     load_plane(z0);
+    cp_async_wait_none();
+    __syncthreads();
   }
   bool touch = false;  // this thread saw two face-adjacent foreground voxels with different labels
   for (int z = z0; z <= z1 + 1; ++z) {
@@ -543,15 +562,11 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
       if (TMA) {
         if (z == z0) ok = mbar_wait(&bar[slot_of(z - 1)], parity_of(z - 1), wt.limit_ns);
         ok = ok && mbar_wait(&bar[slot_of(z)], parity_of(z), wt.limit_ns);
-      } else {
+      } else if (z + 1 <= z1) {
         // plane z + 1 (into the slot plane z - 3 left in the last iteration)
-        // flies while this plane is worked on; plane z has landed once at
-        // most the newest group is pending, and the barrier shows every
-        // thread's copies
-        if (z + 1 <= z1) load_plane(z + 1);
-        else cp_async_commit();
-        cp_async_wait_but_one();
-        __syncthreads();
+        // flies while this plane is worked on; each thread waits for its
+        // copies before the plane barrier below, which shows them all
+        load_plane(z + 1);
       }
     }
     // stage 1, every voxel of plane z: clear LT2, label check, compaction.
@@ -684,6 +699,7 @@ __device__ __forceinline__ void ridge_body(RidgeSmem<NDIM>& sm, const CUtensorMa
       nkept_s[z % 3] = 0;        // plane z - 3's count: read in iteration z - 1, refilled in z + 1
     }
     if (lane == 0) wrec[z & 1][warp] = appended;
+    if (!TMA) cp_async_wait_none();  // plane z + 1 has landed (this thread's part)
     // the one barrier of the plane; it also agrees on a timed-out wait
     if (__syncthreads_or(!ok)) {
       // record the timeout, wait (again bounded) for the copies this CTA
