@@ -145,7 +145,7 @@ def algorithmic_bytes(name, n, n_surv):
 # DRAM bytes (read + write) per launch from one ncu capture (dram__bytes_read
 # and _write, one pass) of the current kernels on the 512^3 particle volume;
 # valid for that workload only.
-TRAFFIC = {"particles_3d_512": {"edt_rows_x": 341684224, "edt_cols_y": 752073045, "edt_cols_z": 1009308416, "lt_ridge": 1810017707, "lt_paint": 1878676821, "shape_reduce": 896730368}}
+TRAFFIC = {"particles_3d_512": {"edt_rows_x": 341698304, "edt_cols_y": 752080384, "edt_cols_z": 1009333333, "lt_ridge": 1817653589, "lt_paint": 1923266389, "shape_reduce": 896663893}}
 
 
 def _probe_lib():
