@@ -153,9 +153,17 @@ __device__ __forceinline__ uint32_t lt_bin16(uint32_t t, uint32_t mx) {
   return (uint32_t)b;
 }
 
-// The same bin with the object's 256 / mx precomputed (rmx): the float
-// estimate floor(sqrt(t * rmx)) is within one of b, and the two integer
-// checks are exact in 32 bits (b^2 <= 256, mx < 2^24, 256 t < 2^32).
+// The same bin from a float estimate e of 16 sqrt(t / mx) that is within
+// one of it (from sqrt(t * 256 / mx), or from sqrtf(t) times 16 / sqrtf(mx)):
+// two integer checks then make it exact, in 32 bits (b^2 <= 256, mx < 2^24,
+// 256 t < 2^32).
+__device__ __forceinline__ uint32_t lt_bin16_e(uint32_t t, uint32_t mx, float e) {
+  uint32_t b = min(15u, (uint32_t)e);
+  const uint32_t T = 256u * t;
+  if (b < 15u && (b + 1) * (b + 1) * mx <= T) ++b;
+  if (b > 0u && b * b * mx > T) --b;
+  return b;
+}
 __device__ __forceinline__ uint32_t lt_bin16_r(uint32_t t, uint32_t mx, float rmx) {
   uint32_t b = min(15u, (uint32_t)sqrtf((float)t * rmx));
   const uint32_t T = 256u * t;
@@ -461,13 +469,14 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
         const bool s = left != l || right != l || comp(Ym, k) != l || comp(Yp, k) != l || comp(Lm, k) != l ||
                        comp(Lp, k) != l;
         const uint32_t t = comp(T, k);
-        const uint32_t qq = __float2uint_rn(sqrtf((float)t) * kFixScale);
+        const float st = sqrtf((float)t);
+        const uint32_t qq = __float2uint_rn(st * kFixScale);
         if (l != cl) {
           flush();
           cl = l;
           if (HIST) {
             mref = max(ref_max[l], 1u);
-            rref = 256.0f / (float)mref;
+            rref = 16.0f / sqrtf((float)mref);
           }
         }
         ++cnt;
@@ -476,7 +485,7 @@ __device__ __forceinline__ void shape_reduce_z_body(const uint32_t* __restrict__
         q += qq;
         qs += s ? qq : 0ull;
         if (HIST) {
-          const uint32_t b = (s ? 16u : 0u) + lt_bin16_r(t, mref, rref);
+          const uint32_t b = (s ? 16u : 0u) + lt_bin16_e(t, mref, st * rref);
           atomicAdd(&hs[b * 256 + tid], 1u);  // the thread's own counter: no conflicts
           used |= 1u << b;
         }
