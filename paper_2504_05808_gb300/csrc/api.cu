@@ -352,16 +352,17 @@ static size_t host_layout(const Dims& d, uint32_t n_labels, size_t off[6]) {
 
 constexpr int kHostSlabs = 8;  // z-slabs of the mask copy in lt_measure_host
 
-// One non-blocking copy stream per device, created on first use and kept.
-static cudaStream_t copy_stream() {
+// Non-blocking helper streams per device, created on first use and kept:
+// which = 0 the copy stream, 1 a second work stream.
+static cudaStream_t helper_stream(int which) {
   static std::mutex mu;
-  static cudaStream_t streams[64] = {nullptr};
+  static cudaStream_t streams[2][64] = {{nullptr}};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> g(mu);
-  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
-    streams[dev] = nullptr;
-  return streams[dev];
+  cudaStream_t& st = streams[which][dev];
+  if (!st && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+  return st;
 }
 
 size_t lt_measure_host_workspace_size(uint32_t n_labels, int ndim, int64_t nx, int64_t ny, int64_t nz) {
@@ -395,16 +396,20 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
   // arrives in z-slabs, each slab's x and y EDT passes start as soon as it
   // is there; the labels arrive in z-slabs during the EDT, and the ridge
   // pass runs slab by slab as they land (a slab also needs the next slab's
-  // first plane). Painting needs every centre (and the `touch` flag of the
-  // whole volume), so it starts after the last ridge slab.
-  cudaStream_t c = copy_stream();
-  if (!c) return LT_ERR_CUDA;
+  // first plane), alternating between `stream` and a second work stream:
+  // slabs are independent (their own LT2 planes, records appended by
+  // atomics), and one slab's launch is too small to fill the GPU alone. The
+  // last two slabs are one ridge chunk each, since they run after the last
+  // copy. Painting needs every centre (and the `touch` flag of the whole
+  // volume), so it starts after the last ridge slab on both streams.
+  cudaStream_t c = helper_stream(0), s2 = helper_stream(1);
+  if (!c || !s2) return LT_ERR_CUDA;
   const Tuning tu;
   const int K = d.ndim == 3 ? std::min(d.nz, kHostSlabs) : 1;
   const int rz = ridge_chunk(tu), nch = (d.nz + rz - 1) / rz;
   const int KL = d.ndim == 3 ? std::min(nch, kHostSlabs) : 1;  // label slabs: whole ridge chunks
-  cudaEvent_t ev[2 * kHostSlabs + 1];
-  const int nev = K + KL + 1;
+  cudaEvent_t ev[2 * kHostSlabs + 3];
+  const int nev = K + KL + 3;
   for (int k = 0; k < nev; ++k)
     if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
       for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
@@ -412,9 +417,16 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
     }
   cudaEvent_t* ev_mask = ev;
   cudaEvent_t* ev_lab = ev + K;
-  cudaEvent_t ev_start = ev[K + KL];
+  cudaEvent_t ev_start = ev[K + KL], ev_edt = ev[K + KL + 1], ev_s2 = ev[K + KL + 2];
   const size_t plane = (size_t)d.nx * d.ny;
-  auto lab_z = [&](int k) { return d.ndim == 3 ? std::min(d.nz, (int)((int64_t)nch * k / KL) * rz) : 0; };
+  // label slab k starts at ridge chunk c0[k]: the last two slabs one chunk
+  // each, the others shared out evenly
+  int c0[kHostSlabs + 1];
+  for (int k = 0; k <= KL; ++k) {
+    const int tail = std::min(KL - 1, 2), head = KL - tail;
+    c0[k] = k <= head ? (int)((int64_t)(nch - tail) * k / head) : (nch - tail) + (k - head);
+  }
+  auto lab_z = [&](int k) { return d.ndim == 3 ? std::min(d.nz, c0[k] * rz) : 0; };
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
   void* body = reinterpret_cast<char*>(ws) + sizeof(WsHeader);
   cudaError_t e = cudaEventRecord(ev_start, s);  // the copies start after earlier work on `stream`
@@ -442,10 +454,15 @@ lt_status lt_measure_host(const uint8_t* mask_host, const uint32_t* labels_host,
     if (e == cudaSuccess) e = edt_launch(mask + z0 * plane, dt2 + z0 * plane, dk, body, s, tu, 1);
   }
   if (e == cudaSuccess) e = edt_launch(nullptr, dt2, d, body, s, tu, 2);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_edt, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_edt, 0);
   for (int k = 0; k < KL && e == cudaSuccess; ++k) {
-    e = cudaStreamWaitEvent(s, ev_lab[std::min(k + 1, KL - 1)], 0);  // (copies land in order)
-    if (e == cudaSuccess) e = lt_ridge_launch(dt2, labels, lt2, d, hdr, body, s, tu, lab_z(k), d.ndim == 3 ? lab_z(k + 1) : 1);
+    cudaStream_t w = (k & 1) ? s2 : s;
+    e = cudaStreamWaitEvent(w, ev_lab[std::min(k + 1, KL - 1)], 0);  // (copies land in order)
+    if (e == cudaSuccess) e = lt_ridge_launch(dt2, labels, lt2, d, hdr, body, w, tu, lab_z(k), d.ndim == 3 ? lab_z(k + 1) : 1);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(ev_s2, s2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_s2, 0);
   if (e == cudaSuccess) e = lt_paint_launch(dt2, labels, lt2, d, hdr, body, s, tu);
   if (e == cudaSuccess) e = shape_launch(labels, lt2, n_labels, d, hdr, body, S, R, nullptr, s);
   for (int k = 0; k < nev; ++k) cudaEventDestroy(ev[k]);  // (released once the streams are past them)
