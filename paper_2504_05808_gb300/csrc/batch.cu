@@ -99,7 +99,8 @@ lt_status check_volume(const lt_volume& v, Dims* d) {
   return LT_OK;
 }
 
-// Volumes of one group, the rest run alone; and the table bytes they need.
+// Volumes of the groups (3D volumes whose y and z axes fit the shared-memory
+// column tiles; 2D images), the rest run alone.
 void plan_groups(const std::vector<Dims>& dims, std::vector<Group>* groups, std::vector<int>* single) {
   groups->clear();
   single->clear();
@@ -115,10 +116,19 @@ void plan_groups(const std::vector<Dims>& dims, std::vector<Group>* groups, std:
     else
       single->push_back(i);
   }
-  for (Group* g : {&g3, &g2})
-    if (!g->vols.empty() && (int)g->vols.size() <= kMaxBatchVols) groups->push_back(*g);
-    else
-      for (int v : g->vols) single->push_back(v);
+  // a group's table holds at most kMaxBatchVols volumes: more of one kind
+  // are split into that many groups of near-equal size (each on a branch)
+  for (Group* g : {&g3, &g2}) {
+    const int n = (int)g->vols.size();
+    if (n == 0) continue;
+    const int parts = (n + kMaxBatchVols - 1) / kMaxBatchVols;
+    for (int k = 0; k < parts; ++k) {
+      Group part;
+      part.ndim = g->ndim;
+      part.vols.assign(g->vols.begin() + (int64_t)n * k / parts, g->vols.begin() + (int64_t)n * (k + 1) / parts);
+      groups->push_back(part);
+    }
+  }
 }
 
 size_t volumes_bytes(const std::vector<lt_volume>& vols, const std::vector<Dims>& dims) {

@@ -148,3 +148,22 @@ def test_batch_reports_device_errors(lt):
         batch.status()
     assert e.value.status == 5
     batch.close()
+
+
+def test_more_volumes_than_one_group_holds(lt):
+    """300 small 3D volumes and 260 small 2D images: more of each kind than one
+    group's table holds (256), so each kind is split into several groups on
+    their own branches; every volume still equals a single call bit for bit."""
+    import torch
+    rng = np.random.default_rng(11)
+    vols = [_blobs(tuple(int(e) for e in rng.integers(6, 20, 3)), 100 + i) for i in range(300)]
+    vols += [_blobs(tuple(int(e) for e in rng.integers(8, 40, 2)), 500 + i) for i in range(260)]
+    ref = [single(lt, *v) for v in vols]
+    items = [make_item(*v) for v in vols]
+    batch = lt.Batch(items, branches=2)
+    batch.run()
+    batch.status()
+    torch.cuda.synchronize()
+    for a, b in zip(items, ref):
+        same(a, b)
+    batch.close()
